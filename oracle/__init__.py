@@ -1,0 +1,153 @@
+"""CPU oracle for the CudaChain convex hull -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does: the
+CUDA path and this oracle share no code.
+
+Contents
+  * ``hull(points)``      -- the definition of the output (strict convex hull
+    vertex indices, CCW, starting at the lexicographic (x, y) minimum, each
+    vertex the smallest index among identical points), by Andrew's monotone
+    chain (the paper's reference [4], Sec. 1) on exact predicates, in C.
+  * ``method(points)``    -- the paper's procedure step by step (Sec. 2.1
+    steps 1-7, Table 1, Sec. 2.1.1, Fig. 2), returning every intermediate set.
+  * ``orient(a, b, c)``   -- the exact orientation predicate used by both.
+  * ``bruteforce``        -- O(n^3) hull and O(n^2) SPA by exact rationals, the
+    pins for the C code.
+
+Parity status: every function here is pinned by tests in ``tests/test_oracle*.py``
+against brute force on exact rationals, closed forms and invariants, except
+the survivor COUNTS of Fig. 11, which the paper prints only as a plot
+(parity unpinned for those counts).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cch_oracle.c")
+_LIB = os.path.join(_HERE, "libcchoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+I32 = 1
+F64 = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (-ffp-contract=off keeps every product
+    and sum separately rounded, which the exact predicate relies on)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            i64, i32p = ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)
+            vp = ctypes.c_void_p
+            lib.oracle_orient_i32.restype = ctypes.c_int
+            lib.oracle_orient_i32.argtypes = [ctypes.c_int32] * 6
+            lib.oracle_orient_f64.restype = ctypes.c_int
+            lib.oracle_orient_f64.argtypes = [ctypes.c_double] * 6
+            lib.oracle_hull_i32.restype = i64
+            lib.oracle_hull_i32.argtypes = [vp, i64, vp]
+            lib.oracle_hull_f64.restype = i64
+            lib.oracle_hull_f64.argtypes = [vp, i64, vp]
+            lib.oracle_method.restype = i64
+            lib.oracle_method.argtypes = [ctypes.c_int, vp, i64] + [vp] * 8
+            del i32p
+            _lib = lib
+    return _lib
+
+
+def _prep(points):
+    p = np.ascontiguousarray(points)
+    if p.ndim != 2 or p.shape[1] != 2:
+        raise ValueError("points must have shape [n, 2]")
+    if p.dtype == np.int32:
+        return p, I32
+    if p.dtype == np.float64:
+        return p, F64
+    raise TypeError(f"unsupported dtype {p.dtype}; use int32 or float64")
+
+
+def orient(a, b, c, dtype=np.float64) -> int:
+    """Exact sign of (b - a) x (c - a): +1 left turn, -1 right turn, 0 collinear."""
+    lib = _load()
+    if np.dtype(dtype) == np.int32:
+        return lib.oracle_orient_i32(int(a[0]), int(a[1]), int(b[0]), int(b[1]),
+                                     int(c[0]), int(c[1]))
+    return lib.oracle_orient_f64(float(a[0]), float(a[1]), float(b[0]), float(b[1]),
+                                 float(c[0]), float(c[1]))
+
+
+def hull(points) -> np.ndarray:
+    """Strict convex hull vertex indices (int32), CCW from the lexicographic
+    (x, y) minimum; ties between identical points resolved to the smallest
+    index.  n = 0 gives an empty array."""
+    p, dt = _prep(points)
+    n = p.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    lib = _load()
+    fn = lib.oracle_hull_i32 if dt == I32 else lib.oracle_hull_f64
+    h = fn(p.ctypes.data, n, out.ctypes.data)
+    return out[:h].copy()
+
+
+def method(points) -> dict:
+    """The paper's procedure step by step; returns the intermediates:
+
+    ``ext``      int32[4]  P_minx, P_miny, P_maxx, P_maxy (E1..E4)
+    ``region``   int8[n]   0 (interior, R0) or 1..4 (Sec. 2.1.1)
+    ``r1``       list of 4 int32 arrays: round-1 survivors per region, index order
+    ``sorted``   list of 4 int32 arrays: the same, sorted per Table 1 (stable)
+    ``spa``      list of 4 int32 arrays: SPA survivors (Fig. 2), sorted order
+    ``hull``     int32[h]  final hull
+    """
+    p, dt = _prep(points)
+    n = p.shape[0]
+    m = max(n, 1)
+    ext = np.full(4, -1, dtype=np.int32)
+    region = np.zeros(m, dtype=np.int8)
+    r1 = np.zeros(m, dtype=np.int32)
+    r1c = np.zeros(4, dtype=np.int64)
+    srt = np.zeros(m, dtype=np.int32)
+    spa = np.zeros(m, dtype=np.int32)
+    spac = np.zeros(4, dtype=np.int64)
+    hl = np.zeros(m, dtype=np.int32)
+    lib = _load()
+    h = lib.oracle_method(dt, p.ctypes.data, n, ext.ctypes.data, region.ctypes.data,
+                          r1.ctypes.data, r1c.ctypes.data, srt.ctypes.data,
+                          spa.ctypes.data, spac.ctypes.data, hl.ctypes.data)
+
+    def split(a, c):
+        out, o = [], 0
+        for k in range(4):
+            out.append(a[o:o + int(c[k])].copy())
+            o += int(c[k])
+        return out
+
+    return {
+        "ext": ext,
+        "region": region[:n].copy(),
+        "r1": split(r1, r1c),
+        "sorted": split(srt, r1c),
+        "spa": split(spa, spac),
+        "hull": hl[:h].copy(),
+    }

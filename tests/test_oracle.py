@@ -1,0 +1,280 @@
+"""Pins for the CPU oracle (no GPU): the oracle is checked against things
+other than itself -- exact rational brute force, closed forms, invariants and
+the worked example of Fig. 4 -- so that a dropped term, a flipped sign or a
+swapped operand in it fails here before it is trusted as the GPU's judge."""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bruteforce as bf
+from paper_1508_05488_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------- predicates
+
+def _near_collinear_f64(rng, m):
+    """Triples whose third point is a rounded point of the line through the
+    first two: the exact orientation is tiny and often of either sign."""
+    out = []
+    for _ in range(m):
+        scale = 2.0 ** int(rng.integers(-30, 30))
+        a = rng.standard_normal(2) * scale
+        b = rng.standard_normal(2) * scale
+        t = rng.standard_normal() * 3
+        c = a + t * (b - a)
+        if rng.random() < 0.3:
+            c = c + np.nextafter(0, 1) * 0 + rng.choice([-1, 1]) * np.spacing(c) * rng.integers(0, 3)
+        out.append((a, b, c))
+    return out
+
+
+def test_orient_f64_matches_exact_rationals():
+    rng = np.random.default_rng(11)
+    cases = _near_collinear_f64(rng, 3000)
+    for _ in range(1000):
+        cases.append(tuple(rng.standard_normal(2) * 10.0 ** rng.integers(-5, 5) for _ in range(3)))
+    # exact collinear dyadic triples and repeated points
+    for _ in range(500):
+        a = rng.integers(-1000, 1000, 2) / 64.0
+        d = rng.integers(-50, 50, 2) / 64.0
+        cases.append((a, a + d, a + rng.integers(-5, 6) * d))
+        cases.append((a, a, a + d))
+    naive_wrong = 0
+    for a, b, c in cases:
+        want = bf.orient(a, b, c)
+        got = oracle.orient(a, b, c)
+        assert got == want, (a, b, c, got, want)
+        naive = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+        naive_wrong += int(np.sign(naive)) != want
+    # the case set must be able to catch an inexact predicate
+    assert naive_wrong > 50
+
+
+def test_orient_f64_extreme_magnitudes():
+    rng = np.random.default_rng(12)
+    for _ in range(500):
+        e = int(rng.integers(-395, 395))
+        a, b = rng.standard_normal(2) * 2.0 ** e, rng.standard_normal(2) * 2.0 ** e
+        c = a + rng.standard_normal() * (b - a)
+        assert oracle.orient(a, b, c) == bf.orient(a, b, c)
+
+
+def test_orient_i32_full_range():
+    rng = np.random.default_rng(13)
+    lo, hi = -2 ** 31, 2 ** 31
+    for _ in range(3000):
+        p = rng.integers(lo, hi, size=6, dtype=np.int64)
+        a, b, c = p[0:2], p[2:4], p[4:6]
+        if rng.random() < 0.3:  # force collinear with a huge span
+            c = a
+        want = bf.orient(a.tolist(), b.tolist(), c.tolist())
+        assert oracle.orient(a, b, c, np.int32) == want
+    # int64 overflow territory: differences of 2^32 - 1
+    a, b, c = (lo, lo), (hi - 1, hi - 1), (lo, hi - 1)
+    assert oracle.orient(a, b, c, np.int32) == 1
+    assert oracle.orient(b, a, c, np.int32) == -1
+
+
+# --------------------------------------------------------------- the hull
+
+@pytest.mark.parametrize("seed", range(160))
+def test_hull_matches_bruteforce(seed):
+    p = inputs.small_cases(seed)
+    assert oracle.hull(p).tolist() == bf.hull(p)
+
+
+def test_hull_empty_single_identical():
+    assert oracle.hull(np.zeros((0, 2))).tolist() == []
+    assert oracle.hull(np.array([[3, 4]], np.int32)).tolist() == [0]
+    p = np.tile(np.array([[1.5, -2.0]]), (7, 1))
+    assert oracle.hull(p).tolist() == [0]
+    # -0.0 and +0.0 are the same coordinate
+    q = np.array([[0.0, 1.0], [-0.0, 1.0], [0.0, -0.0]])
+    assert oracle.hull(q).tolist() == [2, 0]
+
+
+def test_hull_collinear_returns_two_extremes():
+    t = np.arange(50)
+    rng = np.random.default_rng(3)
+    for d in [(1, 2), (1, -3), (0, 1), (1, 0)]:
+        p = np.stack([5 + d[0] * t, 7 + d[1] * t], 1).astype(np.int32)
+        perm = rng.permutation(50)
+        q = p[perm]
+        h = oracle.hull(q).tolist()
+        lo = int(np.argmin(perm)) if d[0] > 0 or (d[0] == 0 and d[1] > 0) else int(np.argmax(perm))
+        assert len(h) == 2
+        assert sorted(map(tuple, q[h].tolist())) == sorted([tuple(p[0]), tuple(p[-1])])
+        assert tuple(q[h[0]]) == min(map(tuple, q.tolist()))
+        del lo
+
+
+def test_hull_regular_polygon_keeps_every_vertex():
+    rng = np.random.default_rng(5)
+    for n in [3, 4, 7, 100, 1000, 20_000]:
+        t = rng.random() + 2 * np.pi * np.arange(n) / n
+        p = np.stack([np.cos(t), np.sin(t)], 1) * 3.0
+        perm = rng.permutation(n)
+        h = oracle.hull(p[perm])
+        assert len(h) == n
+        # CCW from the lexicographic minimum: angles increase cyclically
+        ang = np.unwrap(np.arctan2(p[perm][h][:, 1], p[perm][h][:, 0]))
+        assert np.all(np.diff(ang) > 0)
+
+
+def test_hull_grid_gives_four_corners():
+    for k in [2, 3, 10, 41]:
+        g = np.stack(np.meshgrid(np.arange(k), np.arange(k)), -1).reshape(-1, 2).astype(np.int32)
+        g = g[np.random.default_rng(k).permutation(len(g))]
+        h = oracle.hull(g)
+        assert sorted(map(tuple, g[h].tolist())) == [(0, 0), (0, k - 1), (k - 1, 0), (k - 1, k - 1)]
+        assert tuple(g[h[0]]) == (0, 0) and tuple(g[h[1]]) == (k - 1, 0)
+
+
+def test_hull_parabola_all_vertices_and_square_plus_interior():
+    i = np.arange(-300, 301)
+    p = np.stack([i, i * i], 1).astype(np.int32)
+    assert len(oracle.hull(p)) == len(i)
+    q = np.concatenate([np.array([[0, 0], [10, 0], [10, 10], [0, 10]]),
+                        np.random.default_rng(2).integers(1, 10, (500, 2)),
+                        np.array([[5, 0], [10, 5], [0, 5], [5, 10]])]).astype(np.int32)
+    assert oracle.hull(q).tolist() == [0, 1, 2, 3]
+
+
+def test_hull_circle_config_is_all_extreme():
+    p = inputs.circle_f64(200_000, seed=6)
+    assert len(oracle.hull(p)) == 200_000
+
+
+def _exact_inside_all(p, h):
+    """Every point is on the closed inner side of every hull edge (exact)."""
+    hv = p[h]
+    m = len(h)
+    is_int = p.dtype == np.int32
+    for k in range(m):
+        a, b = hv[k], hv[(k + 1) % m]
+        if is_int:
+            a64, b64, p64 = a.astype(object), b.astype(object), p.astype(object)
+            d = (b64[0] - a64[0]) * (p64[:, 1] - a64[1]) - (b64[1] - a64[1]) * (p64[:, 0] - a64[0])
+            assert all(v >= 0 for v in d)
+        else:
+            d = (b[0] - a[0]) * (p[:, 1] - a[1]) - (b[1] - a[1]) * (p[:, 0] - a[0])
+            scale = (abs(b[0] - a[0]) + abs(b[1] - a[1])) * (np.abs(p).max() + np.abs(a).max()) * 1e-12
+            close = np.nonzero(d < scale)[0]
+            for i in close:
+                assert bf.orient(a, b, p[i]) >= 0
+
+
+@pytest.mark.parametrize("kind", ["i32", "square", "disk", "gauss"])
+def test_hull_invariants_medium(kind):
+    n = 30_000
+    p = {"i32": lambda: inputs.square_i32(n, 9),
+         "square": lambda: inputs.square_f64(n, 9),
+         "disk": lambda: inputs.disk_f64(n, 9),
+         "gauss": lambda: inputs.gauss_f64(n, 9)}[kind]()
+    h = oracle.hull(p)
+    m = len(h)
+    assert m >= 3 and len(set(h.tolist())) == m
+    assert tuple(p[h[0]]) == min(map(tuple, p.tolist()))
+    for k in range(m):  # strictly convex, counter-clockwise
+        assert bf.orient(p[h[k]], p[h[(k + 1) % m]], p[h[(k + 2) % m]]) > 0
+    _exact_inside_all(p, h)
+    # each vertex is the smallest index of its coordinates
+    first = {}
+    for i, q in enumerate(map(tuple, p.tolist())):
+        first.setdefault(q, i)
+    assert all(first[tuple(p[i])] == i for i in h)
+
+
+# ------------------------------------------------------------- the method
+
+@pytest.mark.parametrize("seed", range(120))
+def test_method_stages_match_bruteforce(seed):
+    p = inputs.small_cases(seed)
+    m = oracle.method(p)
+    ext = bf.extremes(p)
+    assert m["ext"].tolist() == ext
+    reg = bf.regions(p, ext)
+    assert m["region"].tolist() == reg
+    for k in range(4):
+        members = [i for i, r in enumerate(reg) if r == k + 1]
+        assert m["r1"][k].tolist() == members                # index order
+        assert sorted(m["sorted"][k].tolist()) == members    # a permutation
+    spa = bf.spa_survivors(p, ext, reg)
+    for k in range(4):
+        assert set(m["spa"][k].tolist()) == spa[k]
+    assert m["hull"].tolist() == bf.hull(p)
+
+
+def _table1_key(p, k, i):
+    x, y = p[i]
+    return [(x, i), (y, i), (-x, i), (-y, i)][k]
+
+
+@pytest.mark.parametrize("kind", ["i32", "square", "disk", "gauss", "degenerate"])
+def test_method_medium(kind):
+    n = 20_000
+    p = {"i32": lambda: inputs.square_i32(n, 21),
+         "square": lambda: inputs.square_f64(n, 21),
+         "disk": lambda: inputs.disk_f64(n, 21),
+         "gauss": lambda: inputs.gauss_f64(n, 21),
+         "degenerate": lambda: inputs.degenerate_f64(n, 21)}[kind]()
+    m = oracle.method(p)
+    h = oracle.hull(p)
+    assert m["hull"].tolist() == h.tolist()
+    pl = p.tolist()
+    for k in range(4):
+        s = m["sorted"][k].tolist()
+        keys = [_table1_key(pl, k, i) for i in s]
+        assert keys == sorted(keys)                           # Table 1 order, stable
+        sp = m["spa"][k].tolist()
+        pos = {i: j for j, i in enumerate(s)}
+        assert [pos[i] for i in sp] == sorted(pos[i] for i in sp)  # subsequence
+    # every hull vertex is an extreme or survives both rounds (Sec. 4.2)
+    kept = set(m["ext"].tolist()).union(*[set(a.tolist()) for a in m["spa"]])
+    assert set(h.tolist()) <= kept
+    # every R0 point is inside or on the quadrilateral (exact)
+    E = [pl[i] for i in m["ext"]] + [pl[m["ext"][0]]]
+    r0 = np.nonzero(m["region"] == 0)[0]
+    rng = np.random.default_rng(0)
+    for i in rng.choice(r0, size=min(300, len(r0)), replace=False):
+        assert all(bf.orient(E[k], E[k + 1], pl[i]) >= 0 for k in range(4))
+
+
+def test_fig4_worked_example():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "fig4_r3_chain.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    labels = [r[0] for r in rows]
+    p = np.array([[int(r[1]), int(r[2])] for r in rows], dtype=np.int32)
+    m = oracle.method(p)
+    lab = lambda idxs: [labels[i] for i in idxs]
+    assert lab(m["ext"]) == ["E1", "E2", "E3", "E4"]
+    assert lab(m["sorted"][2]) == ["P1", "P2", "P3", "P4", "P5", "P6", "P7"]
+    kept = {r[0] for r in rows if r[3] == "1"}
+    assert set(lab(m["spa"][2])) == kept
+    assert lab(m["spa"][2]) == ["P1", "P2", "P5", "P6"]
+    assert all(len(m["r1"][k]) == 0 for k in (0, 1, 3))
+
+
+def test_blocked_spa_of_the_paper_is_a_superset():
+    """Sec. 2.2.2 runs SPA in independent chunks, each restarting t at its
+    chunk's first point; that keeps every point the sequential rule keeps."""
+    p = inputs.disk_f64(50_000, 31)
+    m = oracle.method(p)
+    pl = p.tolist()
+    for k in range(4):
+        s = m["sorted"][k].tolist()
+        c = 1 if k in (0, 2) else 0
+        worse = (lambda v, t: v > t) if k in (0, 3) else (lambda v, t: v < t)
+        blocked = set()
+        for lo in range(0, len(s), 37):
+            t = pl[s[lo]][c]
+            for i in s[lo:lo + 37]:
+                if not worse(pl[i][c], t):
+                    t = pl[i][c]
+                    blocked.add(i)
+        assert set(m["spa"][k].tolist()) <= blocked
