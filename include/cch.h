@@ -1,0 +1,184 @@
+/*
+ * cch.h -- C ABI of the GB300 (sm_103a) CudaChain planar convex hull.
+ *
+ * The library computes the convex hull of planar point sets with the method
+ * of G. Mei, "CudaChain: A Practical GPU-accelerated 2D Convex Hull
+ * Algorithm" (arXiv:1508.05488): the four extreme points and the
+ * quadrilateral discard with region routing (Sec. 2.1 steps 1-3, Sec. 2.1.1),
+ * the per-region sort (step 4, Table 1), the Sorting-based Preprocessing
+ * Approach (step 5, Fig. 2), and the simple polygon's hull (steps 6-7) --
+ * every step on the GPU; the paper's CPU stage (Melkman's algorithm) is
+ * replaced by a device chain-hull stage.
+ *
+ * OUTPUT CONTRACT (all entry points): the vertices of the STRICT convex hull
+ * -- no point that lies on a hull edge between two vertices, no repeated
+ * point -- as int32 indices into the input, counter-clockwise, starting at
+ * the lexicographically smallest point (smallest x, then smallest y).  Among
+ * points with identical coordinates the smallest index is reported.
+ * Degenerate inputs: n = 0 -> no vertex; all points identical -> the one
+ * (smallest) index; all points collinear -> the two end points.
+ *
+ * INPUT CONTRACT: points are a contiguous row-major [n, 2] array of int32 or
+ * float64 (x, y) pairs, aligned to 8 (int32) / 16 (float64) bytes.
+ *   int32   any values; orientation is exact in 64/128-bit integers.
+ *   float64 finite, and each coordinate either 0 or of magnitude in
+ *           [2^-400, 2^400); orientation is exact (filtered, then expansion
+ *           arithmetic).  -0.0 equals +0.0.  A NaN/Inf is reported as
+ *           CCH_ERR_NONFINITE, another value outside the range as
+ *           CCH_ERR_RANGE, in the output count (see below).
+ *   n       0 <= n <= 2^30 points per set, at most 2^31 - 1 in total.
+ *
+ * STREAMS AND OWNERSHIP: entry points taking a `stream` are asynchronous on
+ * that CUDA stream (a cudaStream_t passed as void*; NULL = legacy default
+ * stream).  Device buffers belong to the caller and must stay valid until
+ * the stream reaches the call.  The library keeps one scratch workspace per
+ * stream (device memory, grown on demand, reused by later calls on that
+ * stream); cch_release_workspace() frees it.  Calls on one stream are
+ * serialised by the stream; calls on different streams use different
+ * workspaces and may overlap on the device.
+ *
+ * ERRORS: the return value reports what the host can see before launching
+ * (bad arguments, allocation or launch failure) as a negative CCH_ERR_*
+ * code; nothing is launched then.  Errors found on the device (non-finite or
+ * out-of-range coordinates, an exhausted bounded wait) are written as the
+ * negative code into the set's output count instead of a hull size.
+ */
+#ifndef CCH_H_
+#define CCH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum cch_dtype { CCH_I32 = 1, CCH_F64 = 2 };
+
+enum cch_status {
+  CCH_OK = 0,
+  CCH_ERR_INVALID = -1,    /* bad argument (NULL pointer, n < 0, misaligned) */
+  CCH_ERR_DTYPE = -2,      /* dtype is neither CCH_I32 nor CCH_F64 */
+  CCH_ERR_NONFINITE = -3,  /* a float64 coordinate is NaN or Inf */
+  CCH_ERR_RANGE = -4,      /* size or coordinate magnitude outside the contract */
+  CCH_ERR_NOMEM = -5,      /* device or host allocation failed */
+  CCH_ERR_CUDA = -6,       /* a CUDA runtime call failed */
+  CCH_ERR_TIMEOUT = -7,    /* a bounded device-side wait ran out */
+  CCH_ERR_BUSY = -8,       /* serving: the pending queue is full */
+  CCH_ERR_NOTFOUND = -9    /* serving: unknown ticket */
+};
+
+/* Static description of a status code. */
+const char *cch_status_string(int status);
+
+/*
+ * One hull (Sec. 2.1, steps 1-7).
+ *   points     device pointer to [n, 2] int32 / float64 (see INPUT CONTRACT)
+ *   n          number of points
+ *   dtype      CCH_I32 or CCH_F64
+ *   out_idx    device int32[max(n, 1)]: receives the h hull indices
+ *   out_count  device int32[1]: receives h, or a negative CCH_ERR_* code
+ *   stream     cudaStream_t
+ * Returns CCH_OK once the work is enqueued.
+ */
+int cch_hull(const void *points, int64_t n, int dtype,
+             int32_t *out_idx, int32_t *out_count, void *stream);
+
+/*
+ * Many independent hulls in one launch sequence: set s is
+ * points[offsets[s] .. offsets[s+1]) (offsets: HOST int64[nsets + 1],
+ * offsets[0] = 0, non-decreasing).  Its hull indices are local to the set and
+ * are written to out_idx + offsets[s]; its count (or a negative code) to
+ * out_counts[s].  out_idx: device int32[max(offsets[nsets], 1)];
+ * out_counts: device int32[nsets].  Same method and output contract as
+ * cch_hull per set.
+ */
+int cch_hull_batched(const void *points, const int64_t *offsets, int32_t nsets,
+                     int dtype, int32_t *out_idx, int32_t *out_counts, void *stream);
+
+/*
+ * End-to-end convenience form of cch_hull on HOST buffers: copies the points
+ * to the device (from pinned or pageable host memory), computes the hull and
+ * copies the count and the indices back; returns when they are in host memory.
+ *   points_host  host [n, 2] int32 / float64
+ *   out_idx_host host int32[max(n, 1)]
+ *   out_count    host int32: h or a negative code
+ * Returns CCH_OK or a negative code (the device-side code is also returned).
+ */
+int cch_hull_host(const void *points_host, int64_t n, int dtype,
+                  int32_t *out_idx_host, int32_t *out_count, void *stream);
+
+/*
+ * Intermediate sets of one hull, for stage-by-stage checking.
+ *   opts          bit 0: evaluate every float64 quadrilateral test exactly
+ *                 (no FP32 filter); other bits must be 0
+ *   r1_idx        device int32[max(n,1)]: round-1 survivors (Sec. 2.1.1), in
+ *                 index order, regions interleaved
+ *   r1_region     device int32[max(n,1)]: their regions 1..4
+ *   spa_idx       device int32[max(n,1)]: SPA survivors (Fig. 2) of R1..R4
+ *                 in sorted (Table 1) order, region after region
+ *   counts_host   host int64[10]: s1, records of R1..R4, survivors of R1..R4,
+ *                 and the device status (0 or a negative code)
+ *   out_idx, out_count   as for cch_hull
+ * Synchronises the stream before returning.
+ */
+int cch_hull_stages(const void *points, int64_t n, int dtype, uint32_t opts,
+                    int32_t *r1_idx, int32_t *r1_region, int32_t *spa_idx,
+                    int64_t *counts_host, int32_t *out_idx, int32_t *out_count,
+                    void *stream);
+
+/* Bytes of device scratch one cch_hull call of this size uses. */
+size_t cch_workspace_bytes(int64_t n, int dtype);
+
+/* Free every cached workspace (synchronises the device first). */
+void cch_release_workspace(void);
+
+/* ------------------------------------------------------------ serving --
+ * A server admits hull requests against a device-memory budget, keeps their
+ * inputs and results resident, and batches whatever is admitted into
+ * cch_hull_batched launches on a pool of streams, so that requests arriving
+ * while others run are started as soon as memory and a stream free up.  Its
+ * results are the cch_hull results of each request alone.
+ */
+typedef struct cch_serve_config {
+  size_t budget_bytes;     /* device memory for admitted requests (inputs,
+                              outputs and workspaces); 0 -> 64 GiB */
+  int32_t num_streams;     /* concurrent batches; 0 -> 4 */
+  int32_t max_pending;     /* queue length before CCH_ERR_BUSY; 0 -> 65536 */
+  int32_t max_batch;       /* requests per batch; 0 -> 4096 */
+  int32_t dtype;           /* CCH_I32 or CCH_F64 for every request */
+} cch_serve_config;
+
+typedef struct cch_done {
+  uint64_t ticket;
+  int32_t status;          /* CCH_OK or a negative code */
+  int32_t count;           /* hull size h */
+  const int32_t *idx;      /* HOST pointer to the h indices, valid until
+                              cch_serve_release(ticket) */
+  double latency_ms;       /* submit -> result available */
+} cch_done;
+
+typedef struct cch_server cch_server;
+
+/* Create a server (spawns its scheduler thread). */
+int cch_serve_create(const cch_serve_config *cfg, cch_server **out);
+/* Queue one request; the points (HOST [n,2]) are copied before return.
+ * CCH_ERR_RANGE if the request alone exceeds the budget, CCH_ERR_BUSY if
+ * the queue is full. */
+int cch_serve_submit(cch_server *srv, const void *points, int64_t n, uint64_t *ticket);
+/* Non-blocking: up to `max` finished requests into done[0 .. *n_done). */
+int cch_serve_poll(cch_server *srv, cch_done *done, int max, int *n_done);
+/* Free a finished request's result. */
+int cch_serve_release(cch_server *srv, uint64_t ticket);
+/* Latency and throughput so far: p50/p99 latency (ms) over finished
+ * requests, hulls/s since the first submit. */
+int cch_serve_stats(cch_server *srv, double *p50_ms, double *p99_ms, double *hulls_per_s,
+                    int64_t *finished);
+/* Drain in-flight work, stop the scheduler and free everything. */
+int cch_serve_destroy(cch_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCH_H_ */

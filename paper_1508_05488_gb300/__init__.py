@@ -1,0 +1,239 @@
+"""GB300-native CudaChain: planar convex hulls on the GPU (sm_103a).
+
+Thin ctypes binding over ``libcch.so`` (C ABI in ``include/cch.h``).  The
+binding only marshals arguments: every step of the hull runs in the CUDA
+kernels of ``csrc/``.  There is no CPU fallback -- if the library is missing
+or cannot be loaded, every call raises.
+
+PyTorch supplies device memory and streams; tensors must be contiguous
+``[n, 2]`` int32 or float64 on a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcch.so")
+
+CCH_I32 = 1
+CCH_F64 = 2
+STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported dtype", -3: "non-finite coordinate",
+          -4: "out of range", -5: "out of memory", -6: "CUDA error", -7: "device wait timeout",
+          -8: "server busy", -9: "unknown ticket"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CchError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        super().__init__(f"{what}: {STATUS.get(self.code, 'status')} ({self.code})")
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        lib.cch_status_string.restype = ctypes.c_char_p
+        lib.cch_status_string.argtypes = [ctypes.c_int]
+        lib.cch_hull.restype = ctypes.c_int
+        lib.cch_hull.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
+        lib.cch_hull_batched.restype = ctypes.c_int
+        lib.cch_hull_batched.argtypes = [vp, vp, i32, ctypes.c_int, vp, vp, vp]
+        lib.cch_hull_host.restype = ctypes.c_int
+        lib.cch_hull_host.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
+        lib.cch_hull_stages.restype = ctypes.c_int
+        lib.cch_hull_stages.argtypes = [vp, i64, ctypes.c_int, u32, vp, vp, vp, vp, vp, vp, vp]
+        lib.cch_workspace_bytes.restype = ctypes.c_size_t
+        lib.cch_workspace_bytes.argtypes = [i64, ctypes.c_int]
+        lib.cch_release_workspace.restype = None
+        lib.cch_release_workspace.argtypes = []
+        for name in ("cch_serve_create", "cch_serve_submit", "cch_serve_poll", "cch_serve_release",
+                     "cch_serve_stats", "cch_serve_destroy"):
+            if hasattr(lib, name):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def lib():
+    """The loaded C library (ctypes.CDLL)."""
+    return _load()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise CchError(rc, what)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.int32:
+        return CCH_I32
+    if t.dtype == torch.float64:
+        return CCH_F64
+    raise TypeError(f"points must be int32 or float64, got {t.dtype}")
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_points(points):
+    if not points.is_cuda:
+        raise ValueError("points must be a CUDA tensor (use hull_host for host arrays)")
+    if points.dim() != 2 or points.shape[1] != 2 or not points.is_contiguous():
+        raise ValueError("points must be a contiguous [n, 2] tensor")
+
+
+def hull_async(points, out_idx=None, out_count=None, stream=None):
+    """Enqueue one hull on `stream` (default: current stream).
+
+    Returns (out_idx int32[max(n,1)], out_count int32[1]) device tensors; the
+    first out_count[0] entries of out_idx are the hull indices once the stream
+    reaches them.  A negative count is a device-side error code."""
+    import torch
+    _check_points(points)
+    n = points.shape[0]
+    dev = points.device
+    if out_idx is None:
+        out_idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int32, device=dev)
+    rc = _load().cch_hull(points.data_ptr() if n else None, n, _dtype_code(points),
+                          out_idx.data_ptr(), out_count.data_ptr(), _stream_handle(stream))
+    _check(rc, "cch_hull")
+    return out_idx, out_count
+
+
+def hull(points, stream=None):
+    """Hull vertex indices (int32 CUDA tensor, CCW from the lexicographic
+    minimum).  Synchronises the stream to read the count."""
+    out_idx, out_count = hull_async(points, stream=stream)
+    h = int(out_count.item())
+    if h < 0:
+        raise CchError(h, "cch_hull (device)")
+    return out_idx[:h]
+
+
+def hull_batched_async(points, offsets, out_idx=None, out_counts=None, stream=None):
+    """Enqueue the hulls of sets points[offsets[s]:offsets[s+1]].
+    Returns (out_idx, out_counts) device tensors; set s's indices (local to
+    the set) start at out_idx[offsets[s]]."""
+    import torch
+    _check_points(points)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nsets = off.shape[0] - 1
+    N = int(off[-1]) if nsets >= 0 else 0
+    dev = points.device
+    if out_idx is None:
+        out_idx = torch.empty(max(N, 1), dtype=torch.int32, device=dev)
+    if out_counts is None:
+        out_counts = torch.empty(max(nsets, 1), dtype=torch.int32, device=dev)
+    rc = _load().cch_hull_batched(points.data_ptr() if N else None, off.ctypes.data, nsets,
+                                  _dtype_code(points), out_idx.data_ptr(), out_counts.data_ptr(),
+                                  _stream_handle(stream))
+    _check(rc, "cch_hull_batched")
+    return out_idx, out_counts
+
+
+def hull_batched(points, offsets, stream=None):
+    """List of per-set hull index tensors (synchronises)."""
+    out_idx, out_counts = hull_batched_async(points, offsets, stream=stream)
+    counts = out_counts.cpu().numpy()
+    res = []
+    for s in range(len(offsets) - 1):
+        h = int(counts[s])
+        if h < 0:
+            raise CchError(h, f"cch_hull_batched set {s}")
+        o = int(offsets[s])
+        res.append(out_idx[o:o + h])
+    return res
+
+
+def hull_host(points: np.ndarray, stream=None) -> np.ndarray:
+    """End to end from host memory: copy in, hull, copy out (numpy int32)."""
+    p = np.ascontiguousarray(points)
+    if p.dtype == np.int32:
+        dt = CCH_I32
+    elif p.dtype == np.float64:
+        dt = CCH_F64
+    else:
+        raise TypeError("points must be int32 or float64")
+    n = p.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    cnt = np.zeros(1, dtype=np.int32)
+    rc = _load().cch_hull_host(p.ctypes.data if n else None, n, dt, out.ctypes.data,
+                               cnt.ctypes.data, _stream_handle(stream))
+    _check(rc, "cch_hull_host")
+    return out[:int(cnt[0])].copy()
+
+
+def hull_host_ptr(host_ptr: int, n: int, dtype_code: int, out_idx_ptr: int, out_count_ptr: int,
+                  stream=None) -> int:
+    """cch_hull_host on raw host pointers (e.g. pinned tensors); returns the status."""
+    return _load().cch_hull_host(host_ptr, n, dtype_code, out_idx_ptr, out_count_ptr,
+                                 _stream_handle(stream))
+
+
+def stages(points, exact_only: bool = False, stream=None) -> dict:
+    """Run one hull and return its intermediate sets (synchronises):
+    ``r1`` list of 4 int32 arrays (round-1 survivors per region, index order),
+    ``spa`` list of 4 int32 arrays (SPA survivors per region, sorted order),
+    ``hull`` int32 array, ``counts`` int64[10], ``status``."""
+    import torch
+    _check_points(points)
+    n = points.shape[0]
+    dev = points.device
+    m = max(n, 1)
+    r1 = torch.empty(m, dtype=torch.int32, device=dev)
+    r1r = torch.empty(m, dtype=torch.int32, device=dev)
+    spa = torch.empty(m, dtype=torch.int32, device=dev)
+    out_idx = torch.empty(m, dtype=torch.int32, device=dev)
+    out_count = torch.empty(1, dtype=torch.int32, device=dev)
+    counts = np.zeros(10, dtype=np.int64)
+    rc = _load().cch_hull_stages(points.data_ptr() if n else None, n, _dtype_code(points),
+                                 1 if exact_only else 0, r1.data_ptr(), r1r.data_ptr(),
+                                 spa.data_ptr(), counts.ctypes.data, out_idx.data_ptr(),
+                                 out_count.data_ptr(), _stream_handle(stream))
+    _check(rc, "cch_hull_stages")
+    s1 = int(counts[0])
+    r1_idx = r1[:s1].cpu().numpy()
+    r1_reg = r1r[:s1].cpu().numpy()
+    spa_all = spa[:int(counts[5:9].sum())].cpu().numpy()
+    spa_list, o = [], 0
+    for r in range(4):
+        c = int(counts[5 + r])
+        spa_list.append(spa_all[o:o + c])
+        o += c
+    h = int(out_count.item())
+    return {
+        "r1": [r1_idx[r1_reg == r + 1] for r in range(4)],
+        "r1_counts": counts[1:5].copy(),
+        "spa": spa_list,
+        "hull": out_idx[:max(h, 0)].cpu().numpy(),
+        "count": h,
+        "counts": counts,
+        "status": int(counts[9]),
+    }
+
+
+def workspace_bytes(n: int, dtype_code: int = CCH_F64) -> int:
+    return int(_load().cch_workspace_bytes(n, dtype_code))
+
+
+def release_workspace():
+    _load().cch_release_workspace()

@@ -1,0 +1,411 @@
+// api.cu -- the C ABI (include/cch.h): argument checks, per-stream
+// workspaces, launch planning and the kernel sequence of one call.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "cch.h"
+#include "cch_internal.cuh"
+
+namespace cch {
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Dims {
+  int64_t N;
+  int32_t nsets;
+  int32_t nchunk1;
+  int32_t ntile2;
+  int64_t max_sort_tiles, max_spa_tiles, max_chain_blks, max_out_tiles, Nc;
+};
+
+Dims make_dims(int64_t N, int32_t nsets, int32_t nchunk1, int32_t ntile2) {
+  Dims d;
+  d.N = N;
+  d.nsets = nsets;
+  d.nchunk1 = nchunk1;
+  d.ntile2 = ntile2;
+  d.Nc = N + 8 * (int64_t)nsets;
+  d.max_sort_tiles = N / kSortTile + nsets + 1;
+  d.max_spa_tiles = N / kSpaTile + 4 * (int64_t)nsets + 1;
+  d.max_chain_blks = d.Nc / kChainBlk + 4 * (int64_t)nsets + 1;
+  d.max_out_tiles = d.Nc / kOutTile + 4 * (int64_t)nsets + 1;
+  return d;
+}
+
+// Byte layout of a workspace; `base` null -> sizes only.
+struct Layout {
+  size_t total = 0;
+  size_t ctl_bytes = 0;                  // ctl + ctr (cleared each call)
+  size_t status_off = 0, status_bytes = 0;   // look-back words (cleared on epoch wrap)
+  size_t sets_off = 0;
+  Ws w{};
+};
+
+Layout layout(const Dims& d, char* base) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = up(o + bytes); return base ? base + r : nullptr; };
+  L.w.ctl = (SetCtl*)take(sizeof(SetCtl) * d.nsets);
+  L.w.ctr = (uint32_t*)take(sizeof(uint32_t) * CT_COUNT);
+  L.ctl_bytes = o;
+  L.status_off = o;
+  L.w.st2 = (uint64_t*)take(8 * (size_t)std::max(d.ntile2, 1));
+  L.w.st_sort = (uint64_t*)take(8 * 256 * (size_t)d.max_sort_tiles);
+  L.w.st_spa = (SpaStat*)take(sizeof(SpaStat) * (size_t)d.max_spa_tiles);
+  L.w.st_spa_cnt = (uint64_t*)take(8 * (size_t)d.max_spa_tiles);
+  L.w.st_out = (uint64_t*)take(8 * (size_t)d.max_out_tiles);
+  L.status_bytes = o - L.status_off;
+  L.w.part = (Part*)take(sizeof(Part) * (size_t)std::max(d.nchunk1, 1));
+  L.w.keyA = (uint64_t*)take(8 * (size_t)d.N);
+  L.w.keyB = (uint64_t*)take(8 * (size_t)d.N);
+  L.w.valA = (uint32_t*)take(4 * (size_t)d.N);
+  L.w.valB = (uint32_t*)take(4 * (size_t)d.N);
+  L.w.hist = (uint32_t*)take(4 * (size_t)kSortPasses * 256 * d.nsets);
+  L.w.sort_start = (uint32_t*)take(4 * ((size_t)d.nsets + 1));
+  L.w.spa_start = (uint32_t*)take(4 * (4 * (size_t)d.nsets + 1));
+  L.w.cpts = take(16 * (size_t)d.Nc);
+  L.w.cidx = (uint32_t*)take(4 * (size_t)d.Nc);
+  L.w.cprev = (uint32_t*)take(4 * (size_t)d.Nc);
+  L.w.cnext = (uint32_t*)take(4 * (size_t)d.Nc);
+  L.w.calive = (uint8_t*)take((size_t)d.Nc);
+  L.w.chain_start = (uint32_t*)take(4 * (4 * (size_t)d.nsets + 1));
+  L.w.blk_head = (int32_t*)take(4 * (size_t)d.max_chain_blks);
+  L.w.blk_tail = (int32_t*)take(4 * (size_t)d.max_chain_blks);
+  L.w.out_start = (uint32_t*)take(4 * (4 * (size_t)d.nsets + 1));
+  L.sets_off = o;
+  take(sizeof(SetDesc) * (size_t)d.nsets);
+  L.total = o;
+  return L;
+}
+
+struct Workspace {
+  char* dev = nullptr;
+  size_t bytes = 0;
+  Dims cap{};
+  uint32_t epoch = 0;
+  SetDesc* host_sets = nullptr;      // pinned staging of the set table
+  size_t host_sets_cap = 0;
+  cudaEvent_t sets_done = nullptr;   // staging buffer free again
+  void* h2d = nullptr;               // device copy of host points (cch_hull_host)
+  size_t h2d_bytes = 0;
+  int32_t* dcount = nullptr;         // device counts (cch_hull_host)
+  int32_t* didx = nullptr;
+  size_t didx_bytes = 0;
+};
+
+std::mutex g_mu;
+std::map<cudaStream_t, Workspace*> g_ws;
+int g_sms = 0;
+int g_occ[3] = {0, 0, 0};
+
+int sm_count() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+bool fits(const Dims& c, const Dims& d) {
+  return d.N <= c.N && d.nsets <= c.nsets && d.nchunk1 <= c.nchunk1 && d.ntile2 <= c.ntile2;
+}
+
+// Get (or grow) the workspace of `stream` for dims `d`.  Called with g_mu held.
+int acquire(cudaStream_t stream, const Dims& d, Workspace** out) {
+  Workspace*& ws = g_ws[stream];
+  if (!ws) ws = new Workspace();
+  if (!ws->dev || !fits(ws->cap, d)) {
+    Dims c = d;
+    if (ws->dev) {   // grow by at least 1.5x to amortise
+      c.N = std::max(d.N, ws->cap.N + ws->cap.N / 2);
+      c.nsets = std::max(d.nsets, ws->cap.nsets);
+      c.nchunk1 = std::max(d.nchunk1, ws->cap.nchunk1);
+      c.ntile2 = std::max(d.ntile2, ws->cap.ntile2);
+      c = make_dims(c.N, c.nsets, c.nchunk1, (int32_t)std::max<int64_t>(c.ntile2, c.N / kClsTile + c.nsets + 1));
+      if (cudaStreamSynchronize(stream) != cudaSuccess) return CCH_ERR_CUDA;
+      cudaFree(ws->dev);
+      ws->dev = nullptr;
+    }
+    Layout L = layout(c, nullptr);
+    if (cudaMalloc(&ws->dev, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      ws->dev = nullptr;
+      return CCH_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(ws->dev, 0, L.total, stream) != cudaSuccess) return CCH_ERR_CUDA;
+    ws->bytes = L.total;
+    ws->cap = c;
+    ws->epoch = 0;
+  }
+  *out = ws;
+  return CCH_OK;
+}
+
+int a1_target(int dtype) {
+  int k = dtype == DT_F64 ? 1 : 2;
+  if (!g_occ[k]) g_occ[k] = extremes_blocks_per_sm(dtype);
+  return sm_count() * g_occ[k];
+}
+
+int grid_cap() { return sm_count() * 4; }
+
+// Launch the whole pipeline for the job; `sets_host` is the set table for a
+// batch (nullptr for a single set).  `stages` hooks the stage extraction.
+struct StageOut {
+  int32_t* r1_idx;
+  int32_t* r1_region;
+  int32_t* spa_idx;
+};
+
+int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, StageOut* stages,
+        Workspace** ws_out) {
+  Dims d = make_dims(j.N, j.nsets, j.nchunk1, j.ntile2);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace* ws = nullptr;
+  int st = acquire(stream, d, &ws);
+  if (st != CCH_OK) return st;
+  Layout L = layout(ws->cap, ws->dev);
+  if (++ws->epoch > 0xFFFu) {
+    if (cudaMemsetAsync(ws->dev + L.status_off, 0, L.status_bytes, stream) != cudaSuccess) return CCH_ERR_CUDA;
+    ws->epoch = 1;
+  }
+  j.epoch = ws->epoch;
+  if (cudaMemsetAsync(ws->dev, 0, L.ctl_bytes, stream) != cudaSuccess) return CCH_ERR_CUDA;
+  if (sets_host) {
+    size_t bytes = sizeof(SetDesc) * sets_host->size();
+    if (ws->host_sets_cap < sets_host->size()) {
+      if (ws->host_sets) { cudaEventSynchronize(ws->sets_done); cudaFreeHost(ws->host_sets); }
+      if (cudaMallocHost(&ws->host_sets, bytes) != cudaSuccess) { ws->host_sets = nullptr; ws->host_sets_cap = 0; return CCH_ERR_NOMEM; }
+      ws->host_sets_cap = sets_host->size();
+      if (!ws->sets_done) cudaEventCreateWithFlags(&ws->sets_done, cudaEventDisableTiming);
+    } else if (ws->sets_done) {
+      cudaEventSynchronize(ws->sets_done);
+    }
+    memcpy(ws->host_sets, sets_host->data(), bytes);
+    SetDesc* dsets = reinterpret_cast<SetDesc*>(ws->dev + L.sets_off);
+    if (cudaMemcpyAsync(dsets, ws->host_sets, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return CCH_ERR_CUDA;
+    cudaEventRecord(ws->sets_done, stream);
+    j.sets = dsets;
+  }
+  Launch La{stream, grid_cap()};
+  launch_extremes(j, L.w, La);
+  launch_classify(j, L.w, La);
+  if (stages) launch_extract_r1(j, L.w, stages->r1_idx, stages->r1_region, stream);
+  launch_sort(j, L.w, La);
+  launch_spa(j, L.w, La);
+  launch_chain(j, L.w, La);
+  if (stages) launch_extract_spa(j, L.w, stages->spa_idx, stream);
+  if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
+  if (ws_out) *ws_out = ws;
+  return CCH_OK;
+}
+
+int check_common(const void* points, int64_t n, int dtype, const void* out_idx, const void* out_count) {
+  if (dtype != CCH_I32 && dtype != CCH_F64) return CCH_ERR_DTYPE;
+  if (n < 0 || !out_idx || !out_count) return CCH_ERR_INVALID;
+  if (n > 0 && !points) return CCH_ERR_INVALID;
+  if (n > kMaxSetPoints) return CCH_ERR_RANGE;
+  uintptr_t a = (uintptr_t)points;
+  if (a % (dtype == CCH_F64 ? 16 : 8)) return CCH_ERR_INVALID;
+  return CCH_OK;
+}
+
+// Single-set job.
+Job single_job(const void* points, int64_t n, int dtype, int32_t* out_idx, int32_t* out_count,
+               uint32_t opts) {
+  Job j{};
+  j.pts = points;
+  j.N = n;
+  j.nsets = 1;
+  j.dtype = dtype;
+  j.opts = opts;
+  int target = a1_target(dtype);
+  int64_t len = (n + target - 1) / std::max(target, 1);
+  len = std::max<int64_t>(4096, (len + 1023) / 1024 * 1024);
+  j.chunk1_len = len;
+  int32_t nch = (int32_t)((n + len - 1) / len);
+  j.nchunk1 = nch;
+  j.ntile2 = (int32_t)((n + kClsTile - 1) / kClsTile);
+  j.sets = nullptr;
+  j.one = SetDesc{0, n, 0, nch, 0, j.ntile2};
+  j.out_idx = out_idx;
+  j.out_counts = out_count;
+  return j;
+}
+
+}  // namespace
+}  // namespace cch
+
+using namespace cch;
+
+extern "C" {
+
+const char* cch_status_string(int status) {
+  switch (status) {
+    case CCH_OK: return "ok";
+    case CCH_ERR_INVALID: return "invalid argument";
+    case CCH_ERR_DTYPE: return "unsupported dtype (use CCH_I32 or CCH_F64)";
+    case CCH_ERR_NONFINITE: return "non-finite float64 coordinate";
+    case CCH_ERR_RANGE: return "size or coordinate magnitude outside the supported range";
+    case CCH_ERR_NOMEM: return "out of memory";
+    case CCH_ERR_CUDA: return "CUDA runtime error";
+    case CCH_ERR_TIMEOUT: return "bounded device wait expired";
+    case CCH_ERR_BUSY: return "server queue full";
+    case CCH_ERR_NOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+int cch_hull(const void* points, int64_t n, int dtype, int32_t* out_idx, int32_t* out_count,
+             void* stream) {
+  int st = check_common(points, n, dtype, out_idx, out_count);
+  if (st != CCH_OK) return st;
+  Job j = single_job(points, n, dtype, out_idx, out_count, 0);
+  return run(j, nullptr, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, int dtype,
+                     int32_t* out_idx, int32_t* out_counts, void* stream) {
+  if (dtype != CCH_I32 && dtype != CCH_F64) return CCH_ERR_DTYPE;
+  if (nsets < 0 || !offsets || !out_idx || !out_counts) return CCH_ERR_INVALID;
+  if (nsets == 0) return CCH_OK;
+  if (offsets[0] != 0) return CCH_ERR_INVALID;
+  const int64_t N = offsets[nsets];
+  if (N > 0x7FFFFFFFll) return CCH_ERR_RANGE;
+  if (N > 0 && !points) return CCH_ERR_INVALID;
+  if ((uintptr_t)points % (dtype == CCH_F64 ? 16 : 8)) return CCH_ERR_INVALID;
+  std::vector<SetDesc> sets(nsets);
+  int target = a1_target(dtype);
+  int64_t len = std::max<int64_t>(16384, ((N + target - 1) / std::max(target, 1) + 1023) / 1024 * 1024);
+  int64_t nch = 0, nt = 0;
+  for (int32_t s = 0; s < nsets; s++) {
+    int64_t n = offsets[s + 1] - offsets[s];
+    if (n < 0) return CCH_ERR_INVALID;
+    if (n > kMaxSetPoints) return CCH_ERR_RANGE;
+    int32_t c = (int32_t)((n + len - 1) / len);
+    int32_t t = (int32_t)((n + kClsTile - 1) / kClsTile);
+    sets[s] = SetDesc{offsets[s], n, (int32_t)nch, c, (int32_t)nt, t};
+    nch += c;
+    nt += t;
+  }
+  Job j{};
+  j.pts = points;
+  j.N = N;
+  j.nsets = nsets;
+  j.dtype = dtype;
+  j.nchunk1 = (int32_t)nch;
+  j.ntile2 = (int32_t)nt;
+  j.chunk1_len = len;
+  j.out_idx = out_idx;
+  j.out_counts = out_counts;
+  return run(j, &sets, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int cch_hull_host(const void* points_host, int64_t n, int dtype, int32_t* out_idx_host,
+                  int32_t* out_count, void* stream) {
+  if (dtype != CCH_I32 && dtype != CCH_F64) return CCH_ERR_DTYPE;
+  if (n < 0 || !out_idx_host || !out_count || (n > 0 && !points_host)) return CCH_ERR_INVALID;
+  if (n > kMaxSetPoints) return CCH_ERR_RANGE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t pbytes = (size_t)n * (dtype == CCH_F64 ? 16 : 8);
+  void* dpts = nullptr;
+  int32_t* dcount = nullptr;
+  int32_t* didx = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace*& ws = g_ws[s];
+    if (!ws) ws = new Workspace();
+    if (ws->h2d_bytes < pbytes) {
+      if (ws->h2d) { cudaStreamSynchronize(s); cudaFree(ws->h2d); }
+      ws->h2d = nullptr;
+      ws->h2d_bytes = 0;
+      if (cudaMalloc(&ws->h2d, pbytes) != cudaSuccess) { cudaGetLastError(); return CCH_ERR_NOMEM; }
+      ws->h2d_bytes = pbytes;
+    }
+    size_t ib = 4 * (size_t)std::max<int64_t>(n, 1);
+    if (ws->didx_bytes < ib) {
+      if (ws->didx) { cudaStreamSynchronize(s); cudaFree(ws->didx); }
+      ws->didx = nullptr;
+      ws->didx_bytes = 0;
+      if (cudaMalloc(&ws->didx, ib) != cudaSuccess) { cudaGetLastError(); return CCH_ERR_NOMEM; }
+      ws->didx_bytes = ib;
+    }
+    if (!ws->dcount && cudaMalloc(&ws->dcount, 16) != cudaSuccess) { cudaGetLastError(); return CCH_ERR_NOMEM; }
+    dpts = ws->h2d;
+    dcount = ws->dcount;
+    didx = ws->didx;
+  }
+  if (pbytes && cudaMemcpyAsync(dpts, points_host, pbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return CCH_ERR_CUDA;
+  int st = cch_hull(dpts, n, dtype, didx, dcount, stream);
+  if (st != CCH_OK) return st;
+  if (cudaMemcpyAsync(out_count, dcount, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCH_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CCH_ERR_CUDA;
+  if (*out_count < 0) return *out_count;
+  if (*out_count > 0 &&
+      cudaMemcpyAsync(out_idx_host, didx, 4 * (size_t)*out_count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CCH_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CCH_ERR_CUDA;
+  return CCH_OK;
+}
+
+int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int32_t* r1_idx,
+                    int32_t* r1_region, int32_t* spa_idx, int64_t* counts_host, int32_t* out_idx,
+                    int32_t* out_count, void* stream) {
+  int st = check_common(points, n, dtype, out_idx, out_count);
+  if (st != CCH_OK) return st;
+  if (!r1_idx || !r1_region || !spa_idx || !counts_host) return CCH_ERR_INVALID;
+  if (opts & ~(uint32_t)OPT_NO_FILTER) return CCH_ERR_INVALID;
+  Job j = single_job(points, n, dtype, out_idx, out_count, opts);
+  StageOut so{r1_idx, r1_region, spa_idx};
+  Workspace* ws = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = run(j, nullptr, s, &so, &ws);
+  if (st != CCH_OK) return st;
+  SetCtl c;
+  uint32_t ctr[CT_COUNT];
+  Layout L = layout(ws->cap, ws->dev);
+  if (cudaMemcpyAsync(&c, L.w.ctl, sizeof(SetCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCH_ERR_CUDA;
+  if (cudaMemcpyAsync(ctr, L.w.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCH_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CCH_ERR_CUDA;
+  counts_host[0] = c.s1;
+  for (int r = 0; r < 4; r++) counts_host[1 + r] = c.cnt[r];
+  for (int r = 0; r < 4; r++) counts_host[5 + r] = c.s2[r];
+  counts_host[9] = c.status != 0 ? c.status : (int32_t)ctr[CT_ERR];
+  return CCH_OK;
+}
+
+size_t cch_workspace_bytes(int64_t n, int dtype) {
+  (void)dtype;
+  if (n < 0) return 0;
+  int target = 1216;
+  int64_t len = std::max<int64_t>(4096, ((n + target - 1) / target + 1023) / 1024 * 1024);
+  Dims d = make_dims(n, 1, (int32_t)((n + len - 1) / len), (int32_t)((n + kClsTile - 1) / kClsTile));
+  return layout(d, nullptr).total;
+}
+
+void cch_release_workspace(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaDeviceSynchronize();
+  for (auto& kv : g_ws) {
+    Workspace* ws = kv.second;
+    if (ws->dev) cudaFree(ws->dev);
+    if (ws->host_sets) cudaFreeHost(ws->host_sets);
+    if (ws->sets_done) cudaEventDestroy(ws->sets_done);
+    if (ws->h2d) cudaFree(ws->h2d);
+    if (ws->dcount) cudaFree(ws->dcount);
+    if (ws->didx) cudaFree(ws->didx);
+    delete ws;
+  }
+  g_ws.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,407 @@
+// cch_internal.cuh -- shared device-side definitions of the CudaChain hull
+// pipeline (sm_103a).  Nothing here is visible through the C ABI.
+//
+// Pipeline (Sec. 2.1, steps 1-7), every stage a kernel, every set of points a
+// "set" (a single hull is a batch of one):
+//   a1  k_extremes      four lexicographic extremes + edge set-up (step 1)
+//   a2  k_classify      quadrilateral test, region routing, stable compaction
+//                       of the survivors into one record stream (steps 2-3)
+//   a3  k_sort_hist +   LSD radix sort of the records by the Table 1 key,
+//       k_sort_pass     then by region (step 4)
+//   a4  k_spa           SPA as a segmented exclusive prefix-minimum scan with
+//                       stable compaction into per-region chains (step 5)
+//   a5  k_chain_local + strictly convex chain per region (steps 6-7; the
+//       k_chain_merge + paper's CPU Melkman stage is replaced by chunked
+//       k_output        monotone-chain hulls merged by bridge walks) and the
+//                       output compaction
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cch {
+
+// ------------------------------------------------------------------ status
+enum : int {
+  ST_OK = 0,
+  ST_INVALID = -1,
+  ST_DTYPE = -2,
+  ST_NONFINITE = -3,
+  ST_RANGE = -4,
+  ST_NOMEM = -5,
+  ST_CUDA = -6,
+  ST_TIMEOUT = -7,
+};
+
+enum : int { DT_I32 = 1, DT_F64 = 2 };
+
+// ------------------------------------------------------------------ sizes
+constexpr int kThreads = 256;          // every kernel runs 256-thread CTAs
+constexpr int kWarps = kThreads / 32;
+constexpr int kClsItems = 16;          // points per thread in a2
+constexpr int kClsTile = kThreads * kClsItems;      // 4096 points
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kThreads * kSortItems;    // 4096 records
+constexpr int kSortPasses = 9;         // 8 key bytes + the region digit
+constexpr int kSpaItems = 8;
+constexpr int kSpaTile = kThreads * kSpaItems;      // 2048 records
+constexpr int kChainItems = 16;
+constexpr int kChainBlk = kThreads * kChainItems;   // 4096 chain positions
+constexpr int kOutItems = 16;
+constexpr int kOutTile = kThreads * kOutItems;      // 4096 chain positions
+constexpr uint32_t kIdxMask = (1u << 30) - 1;       // record value: region<<30 | local index
+constexpr int64_t kMaxSetPoints = int64_t(1) << 30;
+
+// set flags
+enum : uint32_t {
+  SF_FILTER = 1u,       // f64: the FP32 filter of a2 is valid for this set
+  SF_WIDE = 2u,         // i32: coordinate spans need 128-bit products
+  SF_EMPTY = 4u,        // n == 0
+  SF_DEGEN0 = 16u,      // bit SF_DEGEN0 << k: E_k and E_{k+1} are the same point
+};
+
+// dynamic-tile and done counters (zeroed every call)
+enum : int {
+  CT_CLS_TILE = 0, CT_CLS_DONE,
+  CT_HIST_TILE, CT_HIST_DONE,
+  CT_SORT_TILE0,                       // + pass
+  CT_SPA_TILE = CT_SORT_TILE0 + kSortPasses, CT_SPA_DONE,
+  CT_OUT_TILE, CT_OUT_DONE,
+  CT_SORT_TOTAL,                       // plan results
+  CT_SPA_TOTAL,
+  CT_CHAIN_TOTAL,
+  CT_OUT_TOTAL,
+  CT_ERR,                              // first device error (negative status)
+  CT_COUNT
+};
+
+// Host-built description of one point set.
+struct SetDesc {
+  int64_t off;          // first point of the set; also the base of its records,
+                        // chain slots (+8 per earlier set) and output slots
+  int64_t n;            // number of points
+  int32_t chunk1;       // first a1 chunk
+  int32_t nchunk1;      // a1 chunks of this set
+  int32_t tile2;        // first a2 tile
+  int32_t ntile2;       // a2 tiles of this set
+};
+
+// Per-call launch description.  A single hull carries its descriptor inline;
+// a batch points at a device array.
+struct Job {
+  const void* pts;      // [N,2] int32 or float64, device
+  int64_t N;            // total points
+  int32_t nsets;
+  int32_t dtype;
+  int32_t nchunk1;      // total a1 chunks
+  int32_t ntile2;       // total a2 tiles
+  int64_t chunk1_len;   // a1 chunk length (points), multiple of 256
+  uint32_t epoch;       // look-back flag epoch of this call (1..0xFFFF)
+  uint32_t opts;        // OPT_* bits
+  const SetDesc* sets;  // device array, or nullptr -> use `one`
+  SetDesc one;
+  int32_t* out_idx;     // device
+  int32_t* out_counts;  // device, [nsets]
+};
+
+enum : uint32_t {
+  OPT_NO_FILTER = 1u,   // force the exact path for every f64 quadrilateral test
+};
+
+__device__ __forceinline__ SetDesc get_set(const Job& j, int s) {
+  return j.sets ? j.sets[s] : j.one;
+}
+
+// Result of a1 for one chunk.
+struct Part {
+  uint64_t k1[4], k2[4];
+  uint32_t idx[4];
+  uint32_t bad;          // 1: non-finite seen, 2: magnitude out of range
+  uint32_t pad;
+};
+
+// Device-resident per-set state (zeroed every call).
+struct SetCtl {
+  uint64_t ek1[4], ek2[4];   // a1 lexicographic keys of E1..E4
+  double   ex[4], ey[4];     // E1..E4 coordinates (int32 widened exactly)
+  float    fA[4], fB[4], fC[4], fE[4];   // FP32 filter of edge k (f64 only)
+  uint32_t eidx[4];          // set-local indices of E1..E4
+  int32_t  status;
+  uint32_t flags;
+  uint32_t arrive1;          // a1 chunk arrivals
+  uint32_t s1;               // round-1 survivors (records)
+  uint32_t cnt[4];           // records per region
+  uint32_t s2[4];            // SPA survivors per region
+};
+
+// SPA prefix-minimum look-back status of one tile: value words published
+// before the flag word (release / acquire).
+struct SpaStat {
+  uint64_t agg_min;
+  uint64_t inc_min;
+  uint32_t flag;             // tag << 16 | kind
+  uint32_t pad;
+};
+
+// Workspace (device pointers), carved from one allocation.
+struct Ws {
+  SetCtl* ctl;               // [nsets]
+  uint32_t* ctr;             // [CT_COUNT]
+  Part* part;                // [nchunk1]
+  uint64_t* st2;             // [ntile2] a2 look-back words
+  uint64_t* keyA; uint32_t* valA;     // [N] records (sort ping)
+  uint64_t* keyB; uint32_t* valB;     // [N] records (sort pong)
+  uint32_t* hist;            // [nsets][kSortPasses][256]
+  uint64_t* st_sort;         // [max_sort_tiles][256] look-back words
+  uint32_t* sort_start;      // [nsets + 1] first sort tile of each set
+  SpaStat* st_spa;           // [max_spa_tiles]
+  uint64_t* st_spa_cnt;      // [max_spa_tiles] survivor-count look-back words
+  uint32_t* spa_start;       // [4 nsets + 1] first SPA tile of (set, region)
+  void* cpts;                // [Nc] chain points (double2 / int2)
+  uint32_t* cidx;            // [Nc] chain point indices (set-local)
+  uint32_t* cprev; uint32_t* cnext;   // [Nc] chain links (chain-relative)
+  uint8_t* calive;           // [Nc]
+  uint32_t* chain_start;     // [4 nsets + 1] first chain block of (set, region)
+  int32_t* blk_head; int32_t* blk_tail;   // [max_chain_blks]
+  uint32_t* out_start;       // [4 nsets + 1] first output tile of (set, region)
+  uint64_t* st_out;          // [max_out_tiles]
+};
+
+// Chain slots of (set s, region r): base + position, positions 0 .. L-1 with
+// position 0 = E_r, L-1 = E_{r+1}, 1 .. L-2 the SPA survivors in order.
+__device__ __forceinline__ int64_t chain_base(const SetDesc& sd, int s, const SetCtl& c, int r) {
+  int64_t b = sd.off + 8 * (int64_t)s + 2 * r;
+  for (int q = 0; q < r; q++) b += c.cnt[q];
+  return b;
+}
+
+// Largest i in [0, n) with a[i] <= v (a non-decreasing, a[0] <= v).
+__device__ __forceinline__ int seg_of(const uint32_t* a, int n, uint32_t v) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (a[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------ order keys
+// Order-preserving unsigned keys: a < b  <=>  key(a) < key(b).
+__device__ __forceinline__ uint64_t key_f64(uint64_t b) {
+  if (b == 0x8000000000000000ull) b = 0;                      // -0.0 == +0.0
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ uint64_t key_i32(int32_t v) {
+  return (uint64_t)((uint32_t)v ^ 0x80000000u);
+}
+
+// a1 domain check of a float64 coordinate: 0, or 2^-400 <= |v| < 2^400.
+// Returns 1 for NaN/Inf, 2 for other out-of-range values.
+__device__ __forceinline__ uint32_t f64_bad(uint64_t b) {
+  uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+  if (e == 0x7FFu) return 1u;
+  if ((b << 1) == 0) return 0u;
+  return (e < 1023u - 400u || e > 1023u + 399u) ? 2u : 0u;
+}
+
+// float64 -> float32 by truncating the significand (integer ops only; the
+// caller guarantees |v| < 2^100).  |v - t| < 2^-23 |v| for |v| >= 2^-126,
+// t = 0 below that.
+__device__ __forceinline__ float f64_trunc_f32(uint64_t b) {
+  uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  uint32_t sign = hi & 0x80000000u;
+  int fe = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  uint32_t f = fe <= 0 ? sign : (sign | ((uint32_t)fe << 23) | m);
+  return __uint_as_float(f);
+}
+
+// --------------------------------------------------- exact orientation
+// orient(a,b,c) = sign((b-a) x (c-a)).
+
+__device__ __forceinline__ int sgn64(long long v) { return (v > 0) - (v < 0); }
+
+__device__ __forceinline__ int orient_i32(int ax, int ay, int bx, int by, int cx, int cy, bool wide) {
+  if (!wide) {
+    // spans < 2^31: each difference fits in 32 bits, each product in 62
+    int dx1 = bx - ax, dy1 = by - ay, dx2 = cx - ax, dy2 = cy - ay;
+    long long d = (long long)dx1 * dy2 - (long long)dy1 * dx2;
+    return sgn64(d);
+  }
+  long long dx1 = (long long)bx - ax, dy1 = (long long)by - ay;
+  long long dx2 = (long long)cx - ax, dy2 = (long long)cy - ay;
+  __int128 d = (__int128)dx1 * dy2 - (__int128)dy1 * dx2;
+  return (d > 0) - (d < 0);
+}
+
+// Error-free transformations (never contracted: explicit _rn intrinsics).
+__device__ __forceinline__ void ef_two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  double bv = __dsub_rn(s, a);
+  double av = __dsub_rn(s, bv);
+  e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+__device__ __forceinline__ void ef_two_prod(double a, double b, double& p, double& e) {
+  p = __dmul_rn(a, b);
+  e = __fma_rn(a, b, -p);
+}
+
+// Exact sign of the 2x2 determinant written as differences of expansions
+// (Shewchuk 1997, orient2d): det = (ax-cx)(by-cy) - (ay-cy)(bx-cx).
+// Every difference is split exactly into head + tail, the eight partial
+// products exactly into value + error, and the sixteen terms are summed
+// with Grow-Expansion; the sign is that of the largest nonzero component.
+static __device__ __noinline__ int orient_f64_exact_tail(double ax, double ay, double bx, double by,
+                                                  double cx, double cy) {
+  double acx, acxt, bcx, bcxt, acy, acyt, bcy, bcyt;
+  ef_two_sum(ax, -cx, acx, acxt);
+  ef_two_sum(bx, -cx, bcx, bcxt);
+  ef_two_sum(ay, -cy, acy, acyt);
+  ef_two_sum(by, -cy, bcy, bcyt);
+  const double L[4] = {acx, acx, acxt, acxt}, Lb[4] = {bcy, bcyt, bcy, bcyt};
+  const double R[4] = {acy, acy, acyt, acyt}, Rb[4] = {bcx, bcxt, bcx, bcxt};
+  double h[17];
+  int m = 0;
+#pragma unroll 1
+  for (int k = 0; k < 8; k++) {
+    double p, e;
+    if (k < 4) ef_two_prod(L[k], Lb[k], p, e);
+    else { ef_two_prod(R[k - 4], Rb[k - 4], p, e); p = -p; e = -e; }
+    double q = e;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; pass++) {
+      for (int i = 0; i < m; i++) {
+        double s, t;
+        ef_two_sum(q, h[i], s, t);
+        h[i] = t;
+        q = s;
+      }
+      h[m++] = q;
+      q = p;
+    }
+  }
+  for (int i = m - 1; i >= 0; i--) {
+    if (h[i] > 0) return 1;
+    if (h[i] < 0) return -1;
+  }
+  return 0;
+}
+
+// FP64 filter with Shewchuk's bound (3 + 16 eps) eps (|l| + |r|), eps = 2^-53,
+// then the exact evaluation.  Valid for coordinates that are 0 or of
+// magnitude in [2^-400, 2^400] (no underflow or overflow anywhere).
+__device__ __forceinline__ int orient_f64(double ax, double ay, double bx, double by,
+                                          double cx, double cy) {
+  double l = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
+  double r = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
+  double d = __dsub_rn(l, r);
+  double bound = __dmul_rn(3.3306690738754716e-16, __dadd_rn(fabs(l), fabs(r)));
+  if (d > bound) return 1;
+  if (-d > bound) return -1;
+  if (l == 0.0 && r == 0.0) return 0;
+  return orient_f64_exact_tail(ax, ay, bx, by, cx, cy);
+}
+
+// ------------------------------------------------- memory-order helpers
+__device__ __forceinline__ uint64_t ld_acq_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acq_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Packed look-back word: [epoch:16 | kind:16 | value:32]; kind 1 = tile
+// aggregate, 2 = inclusive prefix.  A word from an older call or pass has a
+// different epoch/kind tag and reads as "not ready".
+__device__ __forceinline__ uint64_t lb_pack(uint32_t tag, uint32_t kind, uint32_t v) {
+  return ((uint64_t)((tag << 16) | kind) << 32) | v;
+}
+
+constexpr uint32_t kSpinLimit = 1u << 20;   // bounded waits (well under a second per wait)
+
+__device__ __forceinline__ void record_error(uint32_t* ctr, int st) {
+  atomicCAS(reinterpret_cast<int*>(ctr + CT_ERR), 0, st);
+}
+
+// One step of a bounded wait: false once the wait must be abandoned (its own
+// limit ran out, recorded as ST_TIMEOUT, or another wait of the call already
+// failed).
+__device__ __forceinline__ bool spin_step(uint32_t& spins, uint32_t* ctr) {
+  if (++spins > kSpinLimit) {
+    record_error(ctr, ST_TIMEOUT);
+    return false;
+  }
+  if ((spins & 63u) == 0 && *(volatile uint32_t*)(ctr + CT_ERR) != 0) return false;
+  __nanosleep(64);
+  return true;
+}
+
+// Warp-cooperative decoupled look-back over packed count words (sum).
+// Called by all 32 lanes of one warp; returns the exclusive prefix of
+// `tile` over tiles [first, tile).  Tiles before `first` count as zero.
+__device__ __forceinline__ uint32_t lookback_sum(const uint64_t* st, int64_t tile, int64_t first,
+                                                 uint32_t tag, uint32_t* ctr) {
+  const int lane = threadIdx.x & 31;
+  uint32_t excl = 0;
+  int64_t base = tile - 1;
+  uint32_t spins = 0;
+  while (base >= first) {
+    int64_t t = base - lane;
+    uint64_t w = 0;
+    uint32_t kind = 2;
+    uint32_t v = 0;
+    bool done = false;
+    while (!done) {
+      if (t >= first) {
+        w = ld_acq_u64(st + t);
+        uint32_t hi = (uint32_t)(w >> 32);
+        kind = (hi >> 16) == tag ? (hi & 0xFFFFu) : 0u;
+        v = (uint32_t)w;
+      } else {
+        kind = 2; v = 0;
+      }
+      done = __all_sync(0xFFFFFFFFu, kind != 0);
+      if (!done) {
+        bool go = spin_step(spins, ctr);   // identical in every lane
+        if (!__all_sync(0xFFFFFFFFu, go)) return excl;
+      }
+    }
+    uint32_t incl = __ballot_sync(0xFFFFFFFFu, kind == 2);
+    int stop = incl ? __ffs(incl) - 1 : 31;
+    uint32_t add = lane <= stop ? v : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xFFFFFFFFu, add, o);
+    excl += add;
+    if (incl) break;
+    base -= 32;
+  }
+  return excl;
+}
+
+// ------------------------------------------------------------ launchers
+// (defined in the kernel translation units, called from the API)
+struct Launch {
+  cudaStream_t stream;
+  int grid_cap;          // persistent-grid CTA cap (SMs x resident CTAs)
+};
+
+void launch_extremes(const Job& j, const Ws& w, const Launch& L);
+void launch_classify(const Job& j, const Ws& w, const Launch& L);
+void launch_sort(const Job& j, const Ws& w, const Launch& L);
+void launch_spa(const Job& j, const Ws& w, const Launch& L);
+void launch_chain(const Job& j, const Ws& w, const Launch& L);
+// stage extraction (cch_hull_stages)
+void launch_extract_r1(const Job& j, const Ws& w, int32_t* r1_idx, int32_t* r1_region, cudaStream_t st);
+void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
+int extremes_blocks_per_sm(int dtype);
+
+}  // namespace cch

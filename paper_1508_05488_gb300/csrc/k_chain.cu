@@ -1,0 +1,377 @@
+// k_chain.cu -- the simple polygon and its hull (Sec. 2.1 steps 6-7).
+//
+// Chain r of a set is E_r, the SPA survivors of region r in sorted order,
+// E_{r+1}.  After SPA the chain is monotone in its Table 1 order (and in the
+// other coordinate), so its part of the hull is the strictly convex chain
+// obtained by keeping only left turns -- Andrew's monotone-chain pass in the
+// frame of that order.  The paper runs Melkman's algorithm on the CPU for
+// this step; here it runs on the device in three kernels:
+//
+//  k_chain_local  per block of 4096 chain positions: identical neighbours are
+//                 dropped (the first index stays), every thread builds the
+//                 convex chain of its 16 positions with a strict left-turn
+//                 stack, and the 256 partial chains are merged pairwise in
+//                 shared memory.  Partial chains are doubly linked lists.
+//  k_chain_merge  merges the block chains of a region pairwise, level by
+//                 level.  A merge walks the tail of the left chain backwards
+//                 and the head of the right chain forwards until the bridge
+//                 makes left turns at both ends; it costs O(1 + removed).
+//  k_output       stable compaction of the surviving positions of the four
+//                 chains of a set (each without its last point) into out_idx.
+#include "cch_internal.cuh"
+
+namespace cch {
+
+template <int DT>
+struct PT;
+template <>
+struct PT<DT_F64> { using T = double2; };
+template <>
+struct PT<DT_I32> { using T = int2; };
+
+template <int DT>
+__device__ __forceinline__ int orient_pts(const typename PT<DT>::T& a, const typename PT<DT>::T& b,
+                                          const typename PT<DT>::T& c, bool wide) {
+  if constexpr (DT == DT_F64) return orient_f64(a.x, a.y, b.x, b.y, c.x, c.y);
+  else return orient_i32(a.x, a.y, b.x, b.y, c.x, c.y, wide);
+}
+
+template <int DT>
+__device__ __forceinline__ bool same_pt(const typename PT<DT>::T& a, const typename PT<DT>::T& b) {
+  return a.x == b.x && a.y == b.y;   // value equality: -0.0 == +0.0
+}
+
+// Merge two adjacent convex chains given by (head, tail) into the left one.
+// prv/nxt/alive/pt are accessed through the accessor `A` (shared or global).
+template <int DT, class A>
+__device__ void merge_chains(A& acc, int& hl, int& tl, int hr, int tr, bool wide) {
+  if (hr < 0) return;
+  if (hl < 0) { hl = hr; tl = tr; return; }
+  int a = tl, b = hr;
+  for (;;) {
+    bool moved = false;
+    while (a != hl && orient_pts<DT>(acc.pt(acc.prv(a)), acc.pt(a), acc.pt(b), wide) <= 0) {
+      acc.kill(a);
+      a = acc.prv(a);
+      moved = true;
+    }
+    while (b != tr && orient_pts<DT>(acc.pt(a), acc.pt(b), acc.pt(acc.nxt(b)), wide) <= 0) {
+      acc.kill(b);
+      b = acc.nxt(b);
+      moved = true;
+    }
+    if (!moved) break;
+  }
+  acc.link(a, b);
+  tl = tr;
+}
+
+template <int DT>
+struct SmemAcc {
+  typename PT<DT>::T* p;
+  uint16_t* pv;
+  uint16_t* nx;
+  uint8_t* al;
+  __device__ __forceinline__ typename PT<DT>::T pt(int i) const { return p[i]; }
+  __device__ __forceinline__ int prv(int i) const { return pv[i]; }
+  __device__ __forceinline__ int nxt(int i) const { return nx[i]; }
+  __device__ __forceinline__ void kill(int i) { al[i] = 0; }
+  __device__ __forceinline__ void link(int a, int b) { nx[a] = (uint16_t)b; pv[b] = (uint16_t)a; }
+};
+
+template <int DT>
+struct GlobAcc {
+  const typename PT<DT>::T* p;   // chain base applied
+  uint32_t* pv;
+  uint32_t* nx;
+  uint8_t* al;
+  __device__ __forceinline__ typename PT<DT>::T pt(int i) const { return p[i]; }
+  __device__ __forceinline__ int prv(int i) const { return (int)pv[i]; }
+  __device__ __forceinline__ int nxt(int i) const { return (int)nx[i]; }
+  __device__ __forceinline__ void kill(int i) { al[i] = 0; }
+  __device__ __forceinline__ void link(int a, int b) { nx[a] = (uint32_t)b; pv[b] = (uint32_t)a; }
+};
+
+template <int DT>
+constexpr size_t chain_local_smem() {
+  return (size_t)kChainBlk * (sizeof(typename PT<DT>::T) + 2 + 2 + 2 + 1) + 2 * kThreads * sizeof(int);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
+  using P = typename PT<DT>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  P* sp = reinterpret_cast<P*>(smem);
+  uint16_t* pv = reinterpret_cast<uint16_t*>(sp + kChainBlk);
+  uint16_t* nx = pv + kChainBlk;
+  uint16_t* stk = nx + kChainBlk;
+  int* gh = reinterpret_cast<int*>(stk + kChainBlk);
+  int* gt = gh + kThreads;
+  uint8_t* al = reinterpret_cast<uint8_t*>(gt + kThreads);
+  __shared__ P pred;
+
+  const uint32_t total = w.ctr[CT_CHAIN_TOTAL];
+  P* cp = reinterpret_cast<P*>(w.cpts);
+  for (uint32_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int g = seg_of(w.chain_start, 4 * j.nsets, b);
+    const int s = g >> 2, r = g & 3;
+    const SetDesc sd = get_set(j, s);
+    const SetCtl& c = w.ctl[s];
+    const bool wide = (c.flags & SF_WIDE) != 0;
+    const uint32_t lb = b - w.chain_start[g];
+    const uint32_t L = c.s2[r] + 2;
+    const int64_t cb = chain_base(sd, s, c, r);
+    const uint32_t p0 = lb * kChainBlk;
+    const int m = (int)min((uint32_t)kChainBlk, L - p0);
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      uint32_t p = p0 + i;
+      P v;
+      if (p == 0 || p == L - 1) {
+        int k = p == 0 ? r : ((r + 1) & 3);
+        if constexpr (DT == DT_F64) { v.x = c.ex[k]; v.y = c.ey[k]; }
+        else { v.x = (int)c.ex[k]; v.y = (int)c.ey[k]; }
+        cp[cb + p] = v;
+        w.cidx[cb + p] = c.eidx[k];
+      } else {
+        v = cp[cb + p];
+      }
+      sp[i] = v;
+    }
+    if (threadIdx.x == 0 && p0 > 0) pred = cp[cb + p0 - 1];
+    __syncthreads();
+
+    // per thread: strict left-turn stack over its 16 positions
+    const int i0 = threadIdx.x * kChainItems;
+    const int i1 = min(m, i0 + kChainItems);
+    int top = 0;
+    for (int i = i0; i < i1; i++) {
+      bool dup;
+      if (i > 0) dup = same_pt<DT>(sp[i], sp[i - 1]);
+      else dup = p0 > 0 && same_pt<DT>(sp[0], pred);
+      if (dup) { al[i] = 0; continue; }
+      while (top >= 2 && orient_pts<DT>(sp[stk[i0 + top - 2]], sp[stk[i0 + top - 1]], sp[i], wide) <= 0) {
+        al[stk[i0 + top - 1]] = 0;
+        top--;
+      }
+      stk[i0 + top++] = (uint16_t)i;
+      al[i] = 1;
+    }
+    for (int q = 0; q + 1 < top; q++) {
+      nx[stk[i0 + q]] = stk[i0 + q + 1];
+      pv[stk[i0 + q + 1]] = stk[i0 + q];
+    }
+    gh[threadIdx.x] = top ? stk[i0] : -1;
+    gt[threadIdx.x] = top ? stk[i0 + top - 1] : -1;
+
+    SmemAcc<DT> acc{sp, pv, nx, al};
+    for (int step = 1; step < kThreads; step <<= 1) {
+      __syncthreads();
+      const int t = threadIdx.x;
+      if ((t & (2 * step - 1)) == 0 && t + step < kThreads && (t + step) * kChainItems < m) {
+        int hl = gh[t], tl = gt[t];
+        merge_chains<DT>(acc, hl, tl, gh[t + step], gt[t + step], wide);
+        gh[t] = hl;
+        gt[t] = tl;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      w.calive[cb + p0 + i] = al[i];
+      if (al[i]) {
+        w.cprev[cb + p0 + i] = p0 + pv[i];
+        w.cnext[cb + p0 + i] = p0 + nx[i];
+      }
+    }
+    if (threadIdx.x == 0) {
+      w.blk_head[b] = gh[0] < 0 ? -1 : (int)(p0 + gh[0]);
+      w.blk_tail[b] = gt[0] < 0 ? -1 : (int)(p0 + gt[0]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_chain_merge(Job j, Ws w) {
+  using P = typename PT<DT>::T;
+  const int nseg = 4 * j.nsets;
+  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const uint32_t b0 = w.chain_start[g];
+    const int B = (int)(w.chain_start[g + 1] - b0);
+    if (B <= 1) continue;
+    const int s = g >> 2, r = g & 3;
+    const SetDesc sd = get_set(j, s);
+    const SetCtl& c = w.ctl[s];
+    const bool wide = (c.flags & SF_WIDE) != 0;
+    const int64_t cb = chain_base(sd, s, c, r);
+    GlobAcc<DT> acc{reinterpret_cast<const P*>(w.cpts) + cb, w.cprev + cb, w.cnext + cb, w.calive + cb};
+    for (int step = 1; step < B; step <<= 1) {
+      for (int q = threadIdx.x; (int64_t)q * 2 * step < B; q += kThreads) {
+        int left = q * 2 * step, right = left + step;
+        if (right >= B) continue;
+        int hl = w.blk_head[b0 + left], tl = w.blk_tail[b0 + left];
+        merge_chains<DT>(acc, hl, tl, w.blk_head[b0 + right], w.blk_tail[b0 + right], wide);
+        w.blk_head[b0 + left] = hl;
+        w.blk_tail[b0 + left] = tl;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_output(Job j, Ws w) {
+  __shared__ uint32_t sh_tile;
+  __shared__ int sh_last;
+  __shared__ uint32_t cnt[kOutItems][kWarps];
+  __shared__ uint32_t sh_excl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t total = w.ctr[CT_OUT_TOTAL];
+  const uint32_t tag = (j.epoch << 4) | 12u;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (;;) {
+    if (threadIdx.x == 0) sh_tile = atomicAdd(w.ctr + CT_OUT_TILE, 1u);
+    __syncthreads();
+    const uint32_t tile = sh_tile;
+    if (tile >= total) break;
+    const int g = seg_of(w.out_start, 4 * j.nsets, tile);
+    const int s = g >> 2, r = g & 3;
+    const SetDesc sd = get_set(j, s);
+    const SetCtl& c = w.ctl[s];
+    const uint32_t lt = tile - w.out_start[g];
+    const uint32_t first = w.out_start[4 * s];
+    const uint32_t last = w.out_start[4 * s + 4] - 1;
+    const uint32_t lim = c.s2[r] + 1;            // positions 0 .. L-2
+    const int64_t cb = chain_base(sd, s, c, r);
+    uint32_t keepm = 0;
+#pragma unroll
+    for (int k = 0; k < kOutItems; k++) {
+      uint32_t p = lt * kOutTile + k * kThreads + threadIdx.x;
+      bool keep = p < lim && w.calive[cb + p];
+      uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+      if (lane == 0) cnt[k][warp] = __popc(b);
+      keepm |= (keep ? 1u : 0u) << k;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      constexpr int per = kOutItems * kWarps / 32;
+      uint32_t loc[per];
+      uint32_t sum = 0;
+#pragma unroll
+      for (int q = 0; q < per; q++) {
+        int f = lane * per + q;
+        loc[q] = cnt[f / kWarps][f % kWarps];
+        sum += loc[q];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t run = x - sum;
+#pragma unroll
+      for (int q = 0; q < per; q++) {
+        int f = lane * per + q;
+        cnt[f / kWarps][f % kWarps] = run;
+        run += loc[q];
+      }
+      const uint32_t agg = __shfl_sync(0xFFFFFFFFu, x, 31);
+      uint32_t excl = 0;
+      if (tile == first) {
+        if (lane == 0) st_rel_u64(w.st_out + tile, lb_pack(tag, 2, agg));
+      } else {
+        if (lane == 0) st_rel_u64(w.st_out + tile, lb_pack(tag, 1, agg));
+        excl = lookback_sum(w.st_out, tile, first, tag, w.ctr);
+        if (lane == 0) st_rel_u64(w.st_out + tile, lb_pack(tag, 2, excl + agg));
+      }
+      if (lane == 0) {
+        sh_excl = excl;
+        if (tile == last) j.out_counts[s] = (int32_t)(excl + agg);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kOutItems; k++) {
+      bool keep = (keepm >> k) & 1u;
+      uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        uint32_t p = lt * kOutTile + k * kThreads + threadIdx.x;
+        uint32_t pos = sh_excl + cnt[k][warp] + __popc(b & lt_mask);
+        j.out_idx[sd.off + pos] = (int32_t)w.cidx[cb + p];
+      }
+    }
+    __syncthreads();
+  }
+  // last CTA out: a device-side error invalidates every result of the call
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sh_last = atomicAdd(w.ctr + CT_OUT_DONE, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (sh_last) {
+    __threadfence();
+    const int err = (int)ld_acq_u32(w.ctr + CT_ERR);
+    if (err != 0)
+      for (int s = threadIdx.x; s < j.nsets; s += kThreads) j.out_counts[s] = err;
+  }
+}
+
+// ---------------------------------------------------- stage extraction
+__global__ void k_extract_r1(Job j, Ws w, int32_t* r1_idx, int32_t* r1_region) {
+  const uint32_t n1 = w.ctl[0].s1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
+    uint32_t v = w.valA[i];
+    r1_idx[i] = (int32_t)(v & kIdxMask);
+    r1_region[i] = (int32_t)(v >> 30) + 1;
+  }
+}
+
+__global__ void k_extract_spa(Job j, Ws w, int32_t* spa_idx) {
+  const SetDesc sd = get_set(j, 0);
+  const SetCtl& c = w.ctl[0];
+  uint32_t o = 0;
+  for (int r = 0; r < 4; r++) {
+    const int64_t cb = chain_base(sd, 0, c, r);
+    const uint32_t m = c.s2[r];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+      spa_idx[o + i] = (int32_t)w.cidx[cb + 1 + i];
+    o += m;
+  }
+}
+
+void launch_extract_r1(const Job& j, const Ws& w, int32_t* r1_idx, int32_t* r1_region, cudaStream_t st) {
+  k_extract_r1<<<256, kThreads, 0, st>>>(j, w, r1_idx, r1_region);
+}
+
+void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st) {
+  k_extract_spa<<<256, kThreads, 0, st>>>(j, w, spa_idx);
+}
+
+void launch_chain(const Job& j, const Ws& w, const Launch& L) {
+  int64_t blks_max = (j.N + 8 * (int64_t)j.nsets) / kChainBlk + 4 * (int64_t)j.nsets;
+  int grid = (int)(blks_max < L.grid_cap ? blks_max : L.grid_cap);
+  if (grid < 1) grid = 1;
+  int gridm = 4 * j.nsets < L.grid_cap ? 4 * j.nsets : L.grid_cap;
+  if (j.dtype == DT_F64) {
+    constexpr size_t sm = chain_local_smem<DT_F64>();
+    static bool once = [] {
+      cudaFuncSetAttribute(k_chain_local<DT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      return true;
+    }();
+    (void)once;
+    k_chain_local<DT_F64><<<grid, kThreads, sm, L.stream>>>(j, w);
+    k_chain_merge<DT_F64><<<gridm, kThreads, 0, L.stream>>>(j, w);
+  } else {
+    constexpr size_t sm = chain_local_smem<DT_I32>();
+    static bool once = [] {
+      cudaFuncSetAttribute(k_chain_local<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      return true;
+    }();
+    (void)once;
+    k_chain_local<DT_I32><<<grid, kThreads, sm, L.stream>>>(j, w);
+    k_chain_merge<DT_I32><<<gridm, kThreads, 0, L.stream>>>(j, w);
+  }
+  k_output<<<grid, kThreads, 0, L.stream>>>(j, w);
+}
+
+}  // namespace cch

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Every comparison is element by element on integer index lists: the hull is
+unique (strict vertices, CCW from the lexicographic minimum, smallest index
+among identical points), so the bar is bit-exact equality.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_1508_05488_gb300 as cch
+from paper_1508_05488_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def gpu_hull(p):
+    return cch.hull(torch.from_numpy(np.ascontiguousarray(p)).to(DEV)).cpu().numpy()
+
+
+def check(p):
+    got = gpu_hull(p)
+    want = oracle.hull(p)
+    assert np.array_equal(got, want), (p.dtype, p.shape, got[:10], want[:10], len(got), len(want))
+    return got
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_empty_single_two_identical():
+    for dt in (np.int32, np.float64):
+        assert len(gpu_hull(np.zeros((0, 2), dt))) == 0
+        assert gpu_hull(np.array([[5, 7]], dt)).tolist() == [0]
+        check(np.array([[5, 7], [1, 2]], dt))
+        check(np.array([[5, 7], [5, 7]], dt))
+        check(np.tile(np.array([[3, -4]], dt), (10_000, 1)))
+
+
+def test_signed_zero_is_one_coordinate():
+    p = np.array([[0.0, 1.0], [-0.0, 1.0], [0.0, -0.0], [1.0, 1.0], [-0.0, 0.0]])
+    check(p)
+
+
+@pytest.mark.parametrize("d", [(1, 2), (1, -3), (0, 1), (1, 0), (-2, 1)])
+def test_collinear(d):
+    t = np.random.default_rng(1).permutation(30_000)
+    p = np.stack([7 + d[0] * t, -9 + d[1] * t], 1)
+    check(p.astype(np.int32))
+    check((p / 8.0).astype(np.float64))
+
+
+def test_grid_and_small_adversarial():
+    for k in (2, 3, 17, 300):
+        g = np.stack(np.meshgrid(np.arange(k), np.arange(k)), -1).reshape(-1, 2)
+        g = g[np.random.default_rng(k).permutation(len(g))]
+        check(g.astype(np.int32))
+        check(g.astype(np.float64) * 0.5)
+    for seed in range(300):
+        check(inputs.small_cases(seed))
+
+
+def test_full_int32_range_uses_wide_products():
+    rng = np.random.default_rng(5)
+    p = rng.integers(-2 ** 31, 2 ** 31, size=(200_000, 2), dtype=np.int64).astype(np.int32)
+    check(p)
+    q = np.array([[-2 ** 31, -2 ** 31], [2 ** 31 - 1, 2 ** 31 - 1], [-2 ** 31, 2 ** 31 - 1],
+                  [2 ** 31 - 1, -2 ** 31], [0, 0], [-2 ** 31, 0]], dtype=np.int32)
+    check(q)
+
+
+# --------------------------------------------------- several tiles, ragged
+
+@pytest.mark.parametrize("n", [4095, 4096, 4097, 100_003, 1_000_001])
+@pytest.mark.parametrize("kind", ["square", "disk", "gauss", "i32", "idisk"])
+def test_random_sizes(kind, n):
+    seed = n % 97
+    p = {"square": lambda: inputs.square_f64(n, seed),
+         "disk": lambda: inputs.disk_f64(n, seed),
+         "gauss": lambda: inputs.gauss_f64(n, seed),
+         "i32": lambda: inputs.square_i32(n, seed),
+         "idisk": lambda: inputs.disk_i32(n, seed)}[kind]()
+    check(p)
+
+
+@pytest.mark.parametrize("n", [3, 1000, 4098, 70_000, 300_000])
+def test_all_extreme_circle(n):
+    p = inputs.circle_f64(n, seed=n)
+    h = check(p)
+    assert len(h) == n
+
+
+def test_degenerate_grid_duplicates():
+    check(inputs.degenerate_f64(400_000, seed=9))
+
+
+def test_shell_and_far_from_origin():
+    check(inputs.shell_f64(300_000, 3))
+    # far from the origin the FP32 filter cannot decide: exact path everywhere
+    check(inputs.square_f64(200_000, 4) + 1.0e7)
+    check(inputs.disk_f64(100_000, 5) * 2.0 ** 70)
+    check(inputs.disk_f64(100_000, 5) * 2.0 ** -300)
+
+
+# ------------------------------------------------------------ stages
+
+@pytest.mark.parametrize("kind", ["square", "disk", "gauss", "i32", "degenerate", "grid"])
+@pytest.mark.parametrize("exact_only", [False, True])
+def test_stage_sets_match_method(kind, exact_only):
+    n = 150_001
+    p = {"square": lambda: inputs.square_f64(n, 11),
+         "disk": lambda: inputs.disk_f64(n, 12),
+         "gauss": lambda: inputs.gauss_f64(n, 13),
+         "i32": lambda: inputs.square_i32(n, 14),
+         "degenerate": lambda: inputs.degenerate_f64(n, 15),
+         "grid": lambda: (np.random.default_rng(3).integers(0, 40, (n, 2)) / 8.0)}[kind]()
+    st = cch.stages(torch.from_numpy(p).to(DEV), exact_only=exact_only)
+    m = oracle.method(p)
+    assert st["status"] == 0
+    for r in range(4):
+        assert np.array_equal(st["r1"][r], m["r1"][r]), ("round 1", r)
+        assert np.array_equal(st["spa"][r], m["spa"][r]), ("SPA", r)
+    assert np.array_equal(st["hull"], m["hull"])
+
+
+# ------------------------------------------------------------ batched
+
+def test_batched_matches_per_set():
+    rng = np.random.default_rng(21)
+    sizes = [0, 1, 2, 3, 5000, 0, 4096, 4097, 70_000, 7, 130_000, 1]
+    parts = []
+    for i, n in enumerate(sizes):
+        kind = i % 3
+        q = (inputs.square_f64(n, i) if kind == 0 else inputs.disk_f64(n, i) if kind == 1
+             else inputs.circle_f64(n, i))
+        parts.append(q)
+    parts[5] = np.zeros((0, 2))
+    p = np.concatenate(parts)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    res = cch.hull_batched(torch.from_numpy(p).to(DEV), off)
+    for s in range(len(sizes)):
+        want = oracle.hull(p[off[s]:off[s + 1]])
+        assert np.array_equal(res[s].cpu().numpy(), want), s
+    del rng
+
+
+def test_batched_int32_many_sets():
+    p, off = inputs.batched_i32(300, seed=3, lo=16, hi=20_000)
+    res = cch.hull_batched(torch.from_numpy(p).to(DEV), off)
+    for s in range(300):
+        assert np.array_equal(res[s].cpu().numpy(), oracle.hull(p[off[s]:off[s + 1]])), s
+
+
+# ------------------------------------------------------------ host e2e, errors
+
+def test_host_entry_point():
+    p = inputs.disk_f64(500_000, 17)
+    assert np.array_equal(cch.hull_host(p), oracle.hull(p))
+    q = inputs.square_i32(300_000, 18)
+    assert np.array_equal(cch.hull_host(q), oracle.hull(q))
+
+
+def test_device_errors_are_reported_in_the_count():
+    p = inputs.square_f64(10_000, 1)
+    p[77, 1] = np.nan
+    _, cnt = cch.hull_async(torch.from_numpy(p).to(DEV))
+    assert int(cnt.item()) == -3
+    p[77, 1] = 2.0 ** 450
+    _, cnt = cch.hull_async(torch.from_numpy(p).to(DEV))
+    assert int(cnt.item()) == -4
+    p[77, 1] = 5e-324
+    _, cnt = cch.hull_async(torch.from_numpy(p).to(DEV))
+    assert int(cnt.item()) == -4
+    # the context stays usable
+    check(inputs.square_f64(10_000, 2))
+
+
+def test_host_errors_return_codes():
+    lib = cch.lib()
+    x = torch.zeros(4, 2, dtype=torch.float64, device=DEV)
+    o = torch.zeros(4, dtype=torch.int32, device=DEV)
+    c = torch.zeros(1, dtype=torch.int32, device=DEV)
+    assert lib.cch_hull(x.data_ptr(), 4, 7, o.data_ptr(), c.data_ptr(), None) == -2
+    assert lib.cch_hull(x.data_ptr(), -1, 2, o.data_ptr(), c.data_ptr(), None) == -1
+    assert lib.cch_hull(x.data_ptr() + 8, 3, 2, o.data_ptr(), c.data_ptr(), None) == -1
+    assert lib.cch_hull(x.data_ptr(), 4, 2, None, c.data_ptr(), None) == -1
+
+
+def test_repeated_calls_and_streams_are_independent():
+    a = inputs.disk_f64(200_000, 31)
+    b = inputs.square_i32(300_000, 32)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    torch.cuda.synchronize()
+    outs = []
+    for _ in range(5):
+        outs.append((cch.hull_async(ta, stream=s1), cch.hull_async(tb, stream=s2)))
+    torch.cuda.synchronize()
+    wa, wb = oracle.hull(a), oracle.hull(b)
+    for (ia, ca), (ib, cb) in outs:
+        assert np.array_equal(ia[:int(ca.item())].cpu().numpy(), wa)
+        assert np.array_equal(ib[:int(cb.item())].cpu().numpy(), wb)
