@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark of the CudaChain hull on GB300.
+
+One step = the hull of each of three 20M-point float64 sets (uniform unit
+square, unit disk, isotropic Gaussian sigma = 1), inputs resident in HBM.
+`value` is Mpoints/s over all ranks (replicas: every rank runs its own hulls);
+the roofline object reports the dominant streaming kernel against the
+measured HBM bandwidth; `e2e` is the same metric through the host entry point
+(H2D of the points and D2H of the result inside the timed region);
+`cpu_baseline` times the CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s (20M-pt hull, % of HBM roofline); batched hulls/s + p99 vs per-call"
+KINDS = ("square", "disk", "gauss")
+WORKLOAD = ("20M float64 points each of: uniform in unit square (seed 2), uniform in unit disk "
+            "(seed 3), isotropic Gaussian sigma=1 (seed 4); one exact hull per distribution per step")
+
+# Per-launch DRAM traffic of the streaming kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, bytes per input point), valid
+# only for the kernel source it was taken on.
+NCU_TRAFFIC = {
+    # kernel: (bytes per point, source file, sha1 of that file when captured)
+    "k_classify": (262.58e6 / 16e6, "paper_1508_05488_gb300/csrc/k_round1.cu", "467cd4530d47e897addd6ce12231c4fac3e921d1"),
+    "k_extremes": (258.86e6 / 16e6, "paper_1508_05488_gb300/csrc/k_round1.cu", "467cd4530d47e897addd6ce12231c4fac3e921d1"),
+}
+
+
+def src_sha1(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"cch_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["active_mask", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, r in rows:
+            for nm, v in zip(names[1:], r[1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm = [r[0] for r in rows]
+        loaded = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def gen_inputs(n, kinds=KINDS):
+    from paper_1508_05488_gb300 import inputs
+    return {k: inputs.headline_f64(k, n) for k in kinds}
+
+
+def cpu_baseline(pts, sample_n):
+    """The C oracle (single thread, as it stands) on the first `sample_n` points of each set."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    tot = 0
+    for k in pts:
+        p = pts[k][:sample_n]
+        oracle.hull(p)
+        tot += len(p)
+    dt = time.perf_counter() - t0
+    return {"value": tot / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_n} points of each of the {len(pts)} sets ({tot} points), C Andrew hull "
+                      f"with exact predicates, one thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on host cores, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1508_05488_gb300 import inputs
+    import oracle
+    oracle.build()
+    n = args.ref_n
+    pts = {k: inputs.headline_f64(k, n) for k in KINDS}
+    for _ in range(args.warmup):
+        for k in KINDS:
+            oracle.hull(pts[k])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k in KINDS:
+            oracle.hull(pts[k])
+    dt = time.perf_counter() - t0
+    v = args.steps * 3 * n / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpoints/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_points_per_set": n, "n_per_hull": n,
+                   "note": "CPU oracle (C Andrew monotone chain, exact predicates) on the box's host core"},
+        "cpu_baseline": {"value": v, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} points of each of the 3 sets per step"},
+        "e2e": {"value": v, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=20_000_000)
+    ap.add_argument("--cpu-n", type=int, default=4_000_000)
+    ap.add_argument("--ref-n", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kinds", default=",".join(KINDS),
+                    help="comma-separated subset of square,disk,gauss (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    kinds = tuple(k for k in args.kinds.split(",") if k)
+    assert kinds and all(k in KINDS for k in kinds), kinds
+
+    import numpy as np
+    import torch
+    import paper_1508_05488_gb300 as cch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    host = gen_inputs(args.n, kinds)
+    dpts = {k: torch.from_numpy(host[k]).to(dev) for k in kinds}
+    outs = {k: (torch.empty(args.n, dtype=torch.int32, device=dev),
+                torch.empty(1, dtype=torch.int32, device=dev)) for k in kinds}
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for k in kinds:
+            cch.hull_async(dpts[k], outs[k][0], outs[k][1], stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard of the timed configuration: counts are hull sizes
+    counts = {k: int(outs[k][1].item()) for k in kinds}
+    assert all(c > 0 for c in counts.values()), counts
+
+    cch.profile(True)
+    cch.profile_read()
+    l0 = cch.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = cch.launch_count() - l0
+    stage_ms, calls = cch.profile_read()
+    cch.profile(False)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    pts_step = len(kinds) * args.n * world
+    value = pts_step / (ms_step * 1e-3) / 1e6
+
+    # roofline of the dominant streaming kernel (one read of the points per launch)
+    hbm, hbm_src = peaks()
+    per_launch = {k: stage_ms[k] / max(calls, 1) for k in ("k_extremes", "k_classify")}
+    dom = max(per_launch, key=per_launch.get)
+    alg_bytes = 16.0 * args.n
+    achieved = alg_bytes / (per_launch[dom] * 1e-3) / 1e9
+    traffic = None
+    if dom in NCU_TRAFFIC:
+        bpp, rel, sha = NCU_TRAFFIC[dom]
+        if src_sha1(rel) == sha:
+            traffic = bpp * args.n
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "peak_source": hbm_src,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "stage_ms_per_hull": {k: v / max(calls, 1) for k, v in stage_ms.items()}}
+
+    # end to end through the host entry point (pinned host inputs)
+    pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in kinds}
+    hidx = {k: torch.empty(args.n, dtype=torch.int32).pin_memory() for k in kinds}
+    hcnt = {k: torch.zeros(1, dtype=torch.int32).pin_memory() for k in kinds}
+
+    def e2e_step():
+        d2h = 0
+        for k in kinds:
+            rc = cch.hull_host_ptr(pinned[k].data_ptr(), args.n, cch.CCH_F64, hidx[k].data_ptr(),
+                                   hcnt[k].data_ptr(), stream=stream)
+            assert rc == 0, rc
+            d2h += 4 + 4 * int(hcnt[k][0])
+        return d2h
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 4)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        d2h = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": pts_step / e2e_s / 1e6, "unit": "Mpoints/s", "h2d_bytes_per_step": len(kinds) * 16 * args.n,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        return 0
+    cpu = None if args.no_cpu else cpu_baseline(host, args.cpu_n)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if kinds == KINDS else f"{args.n} float64 points of {kinds}",
+                   "n_per_hull": args.n, "hulls_per_step": len(kinds),
+                   "hull_sizes": counts, "l2": "inputs larger than L2 (320 MB per set)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

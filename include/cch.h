@@ -111,9 +111,11 @@ int cch_hull_host(const void *points_host, int64_t n, int dtype,
 /*
  * Intermediate sets of one hull, for stage-by-stage checking.
  *   opts          bit 0: evaluate every float64 quadrilateral test exactly
- *                 (no FP32 filter); other bits must be 0
- *   r1_idx        device int32[max(n,1)]: round-1 survivors (Sec. 2.1.1), in
- *                 index order, regions interleaved
+ *                 (no FP32 filter); bit 1: keep every round-1 survivor (no
+ *                 SPA-dominance prefilter, so r1_idx is exactly the paper's
+ *                 R1..R4); other bits must be 0
+ *   r1_idx        device int32[max(n,1)]: round-1 survivors (Sec. 2.1.1),
+ *                 region after region, index order within a region
  *   r1_region     device int32[max(n,1)]: their regions 1..4
  *   spa_idx       device int32[max(n,1)]: SPA survivors (Fig. 2) of R1..R4
  *                 in sorted (Table 1) order, region after region
@@ -126,6 +128,21 @@ int cch_hull_stages(const void *points, int64_t n, int dtype, uint32_t opts,
                     int32_t *r1_idx, int32_t *r1_region, int32_t *spa_idx,
                     int64_t *counts_host, int32_t *out_idx, int32_t *out_count,
                     void *stream);
+
+/*
+ * Stage timing.  cch_profile(1) makes every later call record CUDA events on
+ * its stream around four stages: (0) the extremes pass a1, (1) the
+ * dominance-table sample, (2) the classify pass a2, (3) everything after a2.
+ * cch_profile_read synchronises on the recorded events, writes the summed
+ * milliseconds per stage to stage_ms[0 .. min(4, max_stages)), the number of
+ * calls to *calls (if not NULL), forgets them, and returns the number of
+ * stages (4).  cch_profile(0) stops recording.
+ */
+int cch_profile(int enable);
+int cch_profile_read(double *stage_ms, int max_stages, int64_t *calls);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+uint64_t cch_launch_count(void);
 
 /* Bytes of device scratch one cch_hull call of this size uses. */
 size_t cch_workspace_bytes(int64_t n, int dtype);

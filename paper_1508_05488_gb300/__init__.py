@@ -59,6 +59,12 @@ def _load():
         lib.cch_workspace_bytes.argtypes = [i64, ctypes.c_int]
         lib.cch_release_workspace.restype = None
         lib.cch_release_workspace.argtypes = []
+        lib.cch_profile.restype = ctypes.c_int
+        lib.cch_profile.argtypes = [ctypes.c_int]
+        lib.cch_profile_read.restype = ctypes.c_int
+        lib.cch_profile_read.argtypes = [vp, ctypes.c_int, vp]
+        lib.cch_launch_count.restype = ctypes.c_uint64
+        lib.cch_launch_count.argtypes = []
         for name in ("cch_serve_create", "cch_serve_submit", "cch_serve_poll", "cch_serve_release",
                      "cch_serve_stats", "cch_serve_destroy"):
             if hasattr(lib, name):
@@ -189,8 +195,13 @@ def hull_host_ptr(host_ptr: int, n: int, dtype_code: int, out_idx_ptr: int, out_
                                  _stream_handle(stream))
 
 
-def stages(points, exact_only: bool = False, stream=None) -> dict:
-    """Run one hull and return its intermediate sets (synchronises):
+def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None) -> dict:
+    """Run one hull and return its intermediate sets (synchronises).
+
+    exact_only  every float64 quadrilateral test in exact arithmetic (no FP32 filter)
+    prefilter   drop SPA-dominated points already in round 1 (default); with
+                False the round-1 sets are exactly the paper's R1..R4
+
     ``r1`` list of 4 int32 arrays (round-1 survivors per region, index order),
     ``spa`` list of 4 int32 arrays (SPA survivors per region, sorted order),
     ``hull`` int32 array, ``counts`` int64[10], ``status``."""
@@ -206,7 +217,8 @@ def stages(points, exact_only: bool = False, stream=None) -> dict:
     out_count = torch.empty(1, dtype=torch.int32, device=dev)
     counts = np.zeros(10, dtype=np.int64)
     rc = _load().cch_hull_stages(points.data_ptr() if n else None, n, _dtype_code(points),
-                                 1 if exact_only else 0, r1.data_ptr(), r1r.data_ptr(),
+                                 (1 if exact_only else 0) | (0 if prefilter else 2),
+                                 r1.data_ptr(), r1r.data_ptr(),
                                  spa.data_ptr(), counts.ctypes.data, out_idx.data_ptr(),
                                  out_count.data_ptr(), _stream_handle(stream))
     _check(rc, "cch_hull_stages")
@@ -229,6 +241,29 @@ def stages(points, exact_only: bool = False, stream=None) -> dict:
         "counts": counts,
         "status": int(counts[9]),
     }
+
+
+STAGE_NAMES = ("k_extremes", "k_stairs", "k_classify", "tail")
+
+
+def profile(enable: bool = True):
+    """Record CUDA events around the pipeline stages of every later call."""
+    _check(_load().cch_profile(1 if enable else 0), "cch_profile")
+
+
+def profile_read() -> tuple[dict, int]:
+    """Summed milliseconds per stage since the last read, and the call count."""
+    ms = np.zeros(8, dtype=np.float64)
+    calls = np.zeros(1, dtype=np.int64)
+    k = _load().cch_profile_read(ms.ctypes.data, 8, calls.ctypes.data)
+    if k < 0:
+        raise CchError(k, "cch_profile_read")
+    return {STAGE_NAMES[i]: float(ms[i]) for i in range(k)}, int(calls[0])
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far."""
+    return int(_load().cch_launch_count())
 
 
 def workspace_bytes(n: int, dtype_code: int = CCH_F64) -> int:

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/cch.h): argument checks, per-stream
 // workspaces, launch planning and the kernel sequence of one call.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -55,13 +56,15 @@ Layout layout(const Dims& d, char* base) {
   L.w.ctr = (uint32_t*)take(sizeof(uint32_t) * CT_COUNT);
   L.ctl_bytes = o;
   L.status_off = o;
-  L.w.st2 = (uint64_t*)take(8 * (size_t)std::max(d.ntile2, 1));
   L.w.st_sort = (uint64_t*)take(8 * 256 * (size_t)d.max_sort_tiles);
   L.w.st_spa = (SpaStat*)take(sizeof(SpaStat) * (size_t)d.max_spa_tiles);
   L.w.st_spa_cnt = (uint64_t*)take(8 * (size_t)d.max_spa_tiles);
   L.w.st_out = (uint64_t*)take(8 * (size_t)d.max_out_tiles);
   L.status_bytes = o - L.status_off;
   L.w.part = (Part*)take(sizeof(Part) * (size_t)std::max(d.nchunk1, 1));
+  L.w.tcnt = (uint64_t*)take(8 * (size_t)std::max(d.ntile2, 1));
+  L.w.toff = (uint4*)take(16 * (size_t)std::max(d.ntile2, 1));
+  L.w.small_seg = (uint32_t*)take(4 * 4 * (size_t)d.nsets);
   L.w.keyA = (uint64_t*)take(8 * (size_t)d.N);
   L.w.keyB = (uint64_t*)take(8 * (size_t)d.N);
   L.w.valA = (uint32_t*)take(4 * (size_t)d.N);
@@ -78,6 +81,7 @@ Layout layout(const Dims& d, char* base) {
   L.w.blk_head = (int32_t*)take(4 * (size_t)d.max_chain_blks);
   L.w.blk_tail = (int32_t*)take(4 * (size_t)d.max_chain_blks);
   L.w.out_start = (uint32_t*)take(4 * (4 * (size_t)d.nsets + 1));
+  L.w.stairs = (uint32_t*)take(4 * 4 * (size_t)kStairB * d.nsets);
   L.sets_off = o;
   take(sizeof(SetDesc) * (size_t)d.nsets);
   L.total = o;
@@ -101,6 +105,21 @@ struct Workspace {
 
 std::mutex g_mu;
 std::map<cudaStream_t, Workspace*> g_ws;
+std::atomic<uint64_t> g_launches{0};
+
+// Optional stage timing: CUDA events around the stages of every call, read
+// back (and summed) by cch_profile_read.
+constexpr int kStages = 4;   // a1, stairs, a2, rest of the pipeline
+struct ProfRec { cudaEvent_t ev[kStages + 1]; };
+bool g_prof = false;
+std::vector<ProfRec> g_prof_pending, g_prof_free;
+
+cudaEvent_t* prof_begin(ProfRec& rec) {
+  if (!g_prof) return nullptr;
+  if (!g_prof_free.empty()) { rec = g_prof_free.back(); g_prof_free.pop_back(); }
+  else for (auto& e : rec.ev) cudaEventCreate(&e);
+  return rec.ev;
+}
 int g_sms = 0;
 int g_occ[3] = {0, 0, 0};
 
@@ -129,7 +148,7 @@ int acquire(cudaStream_t stream, const Dims& d, Workspace** out) {
       c.nsets = std::max(d.nsets, ws->cap.nsets);
       c.nchunk1 = std::max(d.nchunk1, ws->cap.nchunk1);
       c.ntile2 = std::max(d.ntile2, ws->cap.ntile2);
-      c = make_dims(c.N, c.nsets, c.nchunk1, (int32_t)std::max<int64_t>(c.ntile2, c.N / kClsTile + c.nsets + 1));
+      c = make_dims(c.N, c.nsets, c.nchunk1, (int32_t)std::max<int64_t>(c.ntile2, c.N / 2048 + c.nsets + 1));
       if (cudaStreamSynchronize(stream) != cudaSuccess) return CCH_ERR_CUDA;
       cudaFree(ws->dev);
       ws->dev = nullptr;
@@ -195,14 +214,26 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
     cudaEventRecord(ws->sets_done, stream);
     j.sets = dsets;
   }
-  Launch La{stream, grid_cap()};
-  launch_extremes(j, L.w, La);
-  launch_classify(j, L.w, La);
-  if (stages) launch_extract_r1(j, L.w, stages->r1_idx, stages->r1_region, stream);
-  launch_sort(j, L.w, La);
-  launch_spa(j, L.w, La);
-  launch_chain(j, L.w, La);
-  if (stages) launch_extract_spa(j, L.w, stages->spa_idx, stream);
+  Launch La{stream, grid_cap(), 2 * sm_count()};
+  ProfRec rec{};
+  cudaEvent_t* ev = prof_begin(rec);
+  int nk = 0;
+  if (ev) cudaEventRecord(ev[0], stream);
+  nk += launch_extremes(j, L.w, La);
+  if (ev) cudaEventRecord(ev[1], stream);
+  nk += launch_stairs(j, L.w, La);
+  if (ev) cudaEventRecord(ev[2], stream);
+  nk += launch_classify(j, L.w, La);
+  if (ev) cudaEventRecord(ev[3], stream);
+  nk += launch_gather(j, L.w, La);
+  if (stages) { launch_extract_r1(j, L.w, stages->r1_idx, stages->r1_region, stream); nk++; }
+  nk += launch_small(j, L.w, La);
+  nk += launch_sort(j, L.w, La);
+  nk += launch_spa(j, L.w, La);
+  nk += launch_chain(j, L.w, La);
+  if (stages) { launch_extract_spa(j, L.w, stages->spa_idx, stream); nk++; }
+  if (ev) { cudaEventRecord(ev[4], stream); g_prof_pending.push_back(rec); }
+  g_launches += (uint64_t)nk;
   if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
   if (ws_out) *ws_out = ws;
   return CCH_OK;
@@ -233,9 +264,11 @@ Job single_job(const void* points, int64_t n, int dtype, int32_t* out_idx, int32
   j.chunk1_len = len;
   int32_t nch = (int32_t)((n + len - 1) / len);
   j.nchunk1 = nch;
-  j.ntile2 = (int32_t)((n + kClsTile - 1) / kClsTile);
+  const int ct = cls_tile(dtype);
+  j.ntile2 = (int32_t)((n + ct - 1) / ct);
+  j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
   j.sets = nullptr;
-  j.one = SetDesc{0, n, 0, nch, 0, j.ntile2};
+  j.one = SetDesc{0, n, 0, nch, 0, j.ntile2, 0, j.nchunk3};
   j.out_idx = out_idx;
   j.out_counts = out_count;
   return j;
@@ -285,16 +318,19 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
   std::vector<SetDesc> sets(nsets);
   int target = a1_target(dtype);
   int64_t len = std::max<int64_t>(16384, ((N + target - 1) / std::max(target, 1) + 1023) / 1024 * 1024);
-  int64_t nch = 0, nt = 0;
+  int64_t nch = 0, nt = 0, n3 = 0;
+  const int ct = cls_tile(dtype);
   for (int32_t s = 0; s < nsets; s++) {
     int64_t n = offsets[s + 1] - offsets[s];
     if (n < 0) return CCH_ERR_INVALID;
     if (n > kMaxSetPoints) return CCH_ERR_RANGE;
     int32_t c = (int32_t)((n + len - 1) / len);
-    int32_t t = (int32_t)((n + kClsTile - 1) / kClsTile);
-    sets[s] = SetDesc{offsets[s], n, (int32_t)nch, c, (int32_t)nt, t};
+    int32_t t = (int32_t)((n + ct - 1) / ct);
+    int32_t c3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
+    sets[s] = SetDesc{offsets[s], n, (int32_t)nch, c, (int32_t)nt, t, (int32_t)n3, c3};
     nch += c;
     nt += t;
+    n3 += c3;
   }
   Job j{};
   j.pts = points;
@@ -303,6 +339,7 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
   j.dtype = dtype;
   j.nchunk1 = (int32_t)nch;
   j.ntile2 = (int32_t)nt;
+  j.nchunk3 = (int32_t)n3;
   j.chunk1_len = len;
   j.out_idx = out_idx;
   j.out_counts = out_counts;
@@ -363,7 +400,7 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   int st = check_common(points, n, dtype, out_idx, out_count);
   if (st != CCH_OK) return st;
   if (!r1_idx || !r1_region || !spa_idx || !counts_host) return CCH_ERR_INVALID;
-  if (opts & ~(uint32_t)OPT_NO_FILTER) return CCH_ERR_INVALID;
+  if (opts & ~(uint32_t)(OPT_NO_FILTER | OPT_NO_PREFILTER)) return CCH_ERR_INVALID;
   Job j = single_job(points, n, dtype, out_idx, out_count, opts);
   StageOut so{r1_idx, r1_region, spa_idx};
   Workspace* ws = nullptr;
@@ -383,12 +420,39 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   return CCH_OK;
 }
 
+int cch_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof = enable != 0;
+  return CCH_OK;
+}
+
+int cch_profile_read(double* stage_ms, int max_stages, int64_t* calls) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!stage_ms || max_stages < 0) return CCH_ERR_INVALID;
+  for (int k = 0; k < max_stages; k++) stage_ms[k] = 0.0;
+  int64_t n = 0;
+  for (auto& rec : g_prof_pending) {
+    if (cudaEventSynchronize(rec.ev[kStages]) != cudaSuccess) return CCH_ERR_CUDA;
+    for (int k = 0; k < kStages && k < max_stages; k++) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, rec.ev[k], rec.ev[k + 1]);
+      stage_ms[k] += ms;
+    }
+    g_prof_free.push_back(rec);
+    n++;
+  }
+  g_prof_pending.clear();
+  if (calls) *calls = n;
+  return kStages;
+}
+
+uint64_t cch_launch_count(void) { return g_launches.load(); }
+
 size_t cch_workspace_bytes(int64_t n, int dtype) {
-  (void)dtype;
-  if (n < 0) return 0;
+  if (n < 0 || (dtype != CCH_I32 && dtype != CCH_F64)) return 0;
   int target = 1216;
   int64_t len = std::max<int64_t>(4096, ((n + target - 1) / target + 1023) / 1024 * 1024);
-  Dims d = make_dims(n, 1, (int32_t)((n + len - 1) / len), (int32_t)((n + kClsTile - 1) / kClsTile));
+  Dims d = make_dims(n, 1, (int32_t)((n + len - 1) / len), (int32_t)((n + cls_tile(dtype) - 1) / cls_tile(dtype)));
   return layout(d, nullptr).total;
 }
 

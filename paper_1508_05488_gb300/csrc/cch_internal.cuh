@@ -37,11 +37,31 @@ enum : int { DT_I32 = 1, DT_F64 = 2 };
 // ------------------------------------------------------------------ sizes
 constexpr int kThreads = 256;          // every kernel runs 256-thread CTAs
 constexpr int kWarps = kThreads / 32;
-constexpr int kClsItems = 16;          // points per thread in a2
-constexpr int kClsTile = kThreads * kClsItems;      // 4096 points
+// a2 tiles are 32 KB of points: 2048 float64 or 4096 int32 points
+constexpr int kClsTileBytes = 32768;
+constexpr int kClsStages = 3;          // TMA ring depth of a2
+__host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048 : 4096; }
+// SPA-dominance prefilter ("stairs"): per region, the prefix minimum of the
+// compared coordinate over buckets of the sort coordinate, built from a
+// sample of the set.
+constexpr int kStairB = 1024;          // buckets per region
+constexpr int64_t kStairSample = int64_t(1) << 20;   // sample points per set (the last ones)
+constexpr int kStairChunk = 8192;      // sample points per CTA
+// Sample of a set: its last m points (the most recently streamed by a1),
+// m = min(n, 2^20, max(8192, n / 16)).
+__host__ __device__ inline int64_t stairs_sample(int64_t n) {
+  int64_t m = n / 16;
+  if (m < kStairChunk) m = kStairChunk;
+  if (m > kStairSample) m = kStairSample;
+  return m < n ? m : n;
+}
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kThreads * kSortItems;    // 4096 records
 constexpr int kSortPasses = 9;         // 8 key bytes + the region digit
+// A set whose four regions each hold at most kSmallMax round-1 survivors is
+// sorted and SPA-scanned by one CTA per region in shared memory.
+constexpr int kSmallMax = 16384;
+constexpr int kSmallThreads = 1024;
 constexpr int kSpaItems = 8;
 constexpr int kSpaTile = kThreads * kSpaItems;      // 2048 records
 constexpr int kChainItems = 16;
@@ -55,13 +75,14 @@ constexpr int64_t kMaxSetPoints = int64_t(1) << 30;
 enum : uint32_t {
   SF_FILTER = 1u,       // f64: the FP32 filter of a2 is valid for this set
   SF_WIDE = 2u,         // i32: coordinate spans need 128-bit products
-  SF_EMPTY = 4u,        // n == 0
+  SF_STAIRS = 4u,       // the dominance prefilter is active for this set
+  SF_BIG = 8u,          // some region exceeds kSmallMax survivors: multi-CTA sort
   SF_DEGEN0 = 16u,      // bit SF_DEGEN0 << k: E_k and E_{k+1} are the same point
 };
 
 // dynamic-tile and done counters (zeroed every call)
 enum : int {
-  CT_CLS_TILE = 0, CT_CLS_DONE,
+  CT_CLS_TILE = 0, CT_CLS_DONE, CT_PLAN_DONE, CT_SMALL_TOTAL,
   CT_HIST_TILE, CT_HIST_DONE,
   CT_SORT_TILE0,                       // + pass
   CT_SPA_TILE = CT_SORT_TILE0 + kSortPasses, CT_SPA_DONE,
@@ -83,6 +104,8 @@ struct SetDesc {
   int32_t nchunk1;      // a1 chunks of this set
   int32_t tile2;        // first a2 tile
   int32_t ntile2;       // a2 tiles of this set
+  int32_t chunk3;       // first stairs chunk
+  int32_t nchunk3;      // stairs chunks of this set
 };
 
 // Per-call launch description.  A single hull carries its descriptor inline;
@@ -94,6 +117,8 @@ struct Job {
   int32_t dtype;
   int32_t nchunk1;      // total a1 chunks
   int32_t ntile2;       // total a2 tiles
+  int32_t nchunk3;      // total stairs chunks
+  int32_t pad0;
   int64_t chunk1_len;   // a1 chunk length (points), multiple of 256
   uint32_t epoch;       // look-back flag epoch of this call (1..0xFFFF)
   uint32_t opts;        // OPT_* bits
@@ -104,7 +129,8 @@ struct Job {
 };
 
 enum : uint32_t {
-  OPT_NO_FILTER = 1u,   // force the exact path for every f64 quadrilateral test
+  OPT_NO_FILTER = 1u,     // force the exact path for every f64 quadrilateral test
+  OPT_NO_PREFILTER = 2u,  // keep every round-1 survivor (the paper's round 1 as printed)
 };
 
 __device__ __forceinline__ SetDesc get_set(const Job& j, int s) {
@@ -131,6 +157,9 @@ struct SetCtl {
   uint32_t s1;               // round-1 survivors (records)
   uint32_t cnt[4];           // records per region
   uint32_t s2[4];            // SPA survivors per region
+  float    slo[4], shi[4], sscale[4];  // stairs bucket map of region r: b = (u - lo) * scale
+  uint32_t arrive3;          // stairs chunk arrivals
+  uint32_t pad1;
 };
 
 // SPA prefix-minimum look-back status of one tile: value words published
@@ -147,7 +176,9 @@ struct Ws {
   SetCtl* ctl;               // [nsets]
   uint32_t* ctr;             // [CT_COUNT]
   Part* part;                // [nchunk1]
-  uint64_t* st2;             // [ntile2] a2 look-back words
+  uint64_t* tcnt;            // [ntile2] survivors of an a2 tile per region (4 x u16)
+  uint4* toff;               // [ntile2] exclusive prefix of tcnt over the set's tiles
+  uint32_t* small_seg;       // [4 nsets] (set, region) segments of the shared-memory path
   uint64_t* keyA; uint32_t* valA;     // [N] records (sort ping)
   uint64_t* keyB; uint32_t* valB;     // [N] records (sort pong)
   uint32_t* hist;            // [nsets][kSortPasses][256]
@@ -164,6 +195,7 @@ struct Ws {
   int32_t* blk_head; int32_t* blk_tail;   // [max_chain_blks]
   uint32_t* out_start;       // [4 nsets + 1] first output tile of (set, region)
   uint64_t* st_out;          // [max_out_tiles]
+  uint32_t* stairs;          // [nsets][4][kStairB] bucket minima, then prefix minima
 };
 
 // Chain slots of (set s, region r): base + position, positions 0 .. L-1 with
@@ -387,18 +419,76 @@ __device__ __forceinline__ uint32_t lookback_sum(const uint64_t* st, int64_t til
   return excl;
 }
 
+// SPA value of a point of region r (0..3): the compared coordinate as an
+// order-preserving key in "smaller is better" form -- R1 y, R2 -x, R3 -y,
+// R4 x (Fig. 2: R1 keeps y <= t, R2 x >= t, R3 y >= t, R4 x <= t).
+__device__ __forceinline__ uint64_t spa_v_f64(double x, double y, int r) {
+  uint64_t kx = key_f64((uint64_t)__double_as_longlong(x));
+  uint64_t ky = key_f64((uint64_t)__double_as_longlong(y));
+  switch (r) {
+    case 0: return ky;
+    case 1: return ~kx;
+    case 2: return ~ky;
+    default: return kx;
+  }
+}
+__device__ __forceinline__ uint64_t spa_v_i32(int x, int y, int r) {
+  uint64_t kx = key_i32(x), ky = key_i32(y);
+  switch (r) {
+    case 0: return ky;
+    case 1: return kx ^ 0xFFFFFFFFull;
+    case 2: return ky ^ 0xFFFFFFFFull;
+    default: return kx;
+  }
+}
+
+// ------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes % 16 == 0),
+// completion signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
 // ------------------------------------------------------------ launchers
 // (defined in the kernel translation units, called from the API)
 struct Launch {
   cudaStream_t stream;
   int grid_cap;          // persistent-grid CTA cap (SMs x resident CTAs)
+  int cls_grid;          // a2 CTAs (2 per SM)
 };
 
-void launch_extremes(const Job& j, const Ws& w, const Launch& L);
-void launch_classify(const Job& j, const Ws& w, const Launch& L);
-void launch_sort(const Job& j, const Ws& w, const Launch& L);
-void launch_spa(const Job& j, const Ws& w, const Launch& L);
-void launch_chain(const Job& j, const Ws& w, const Launch& L);
+// Each returns the number of kernels it launched.
+int launch_extremes(const Job& j, const Ws& w, const Launch& L);
+int launch_stairs(const Job& j, const Ws& w, const Launch& L);
+int launch_classify(const Job& j, const Ws& w, const Launch& L);
+int launch_gather(const Job& j, const Ws& w, const Launch& L);
+int launch_small(const Job& j, const Ws& w, const Launch& L);
+int launch_sort(const Job& j, const Ws& w, const Launch& L);
+int launch_spa(const Job& j, const Ws& w, const Launch& L);
+int launch_chain(const Job& j, const Ws& w, const Launch& L);
 // stage extraction (cch_hull_stages)
 void launch_extract_r1(const Job& j, const Ws& w, int32_t* r1_idx, int32_t* r1_region, cudaStream_t st);
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);

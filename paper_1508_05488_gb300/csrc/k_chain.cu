@@ -347,7 +347,7 @@ void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_
   k_extract_spa<<<256, kThreads, 0, st>>>(j, w, spa_idx);
 }
 
-void launch_chain(const Job& j, const Ws& w, const Launch& L) {
+int launch_chain(const Job& j, const Ws& w, const Launch& L) {
   int64_t blks_max = (j.N + 8 * (int64_t)j.nsets) / kChainBlk + 4 * (int64_t)j.nsets;
   int grid = (int)(blks_max < L.grid_cap ? blks_max : L.grid_cap);
   if (grid < 1) grid = 1;
@@ -372,6 +372,7 @@ void launch_chain(const Job& j, const Ws& w, const Launch& L) {
     k_chain_merge<DT_I32><<<gridm, kThreads, 0, L.stream>>>(j, w);
   }
   k_output<<<grid, kThreads, 0, L.stream>>>(j, w);
+  return 3;
 }
 
 }  // namespace cch

@@ -2,35 +2,80 @@
 //
 //  k_extremes  one streaming pass over the points: the four lexicographic
 //              extremes E1..E4 = P_minx, P_miny, P_maxx, P_maxy (smallest
-//              index on ties), the float64 domain check, and -- in the last
-//              CTA of each set -- the edge set-up for the region test.
-//  k_classify  second streaming pass: the quadrilateral test with region
-//              routing (first k whose directed edge E_k -> E_{k+1} has the
-//              point strictly on its right, i.e. outside), and stable
+//              index on ties) and the float64 domain check; the last CTA of
+//              each set sets up its edges and bucket maps.
+//  k_stairs    the SPA-dominance tables of a sample of each set (see below).
+//  k_classify  second streaming pass, fed by a TMA ring of shared-memory
+//              tiles: the quadrilateral test with region routing (first k
+//              whose directed edge E_k -> E_{k+1} has the point strictly on
+//              its right, i.e. outside), the dominance prefilter, and stable
 //              compaction of the survivors into one record stream per set
 //              (warp ballots, block scan, decoupled look-back).
+//
+// Dominance prefilter.  SPA (Fig. 2) discards a point P of region R_r when a
+// point Q of R_r before P in the Table 1 order has a strictly better compared
+// coordinate (Fig. 3).  If Q is ANY input point strictly before P in the sort
+// coordinate and strictly better in the compared one, Q itself lies in R_r
+// (it is on the outer side of edge r and on the inner side of the earlier
+// edges), so P is not an SPA survivor of the full set and dropping it early
+// leaves the SPA survivors -- and the hull -- unchanged.  k_stairs buckets a
+// sample by the sort coordinate (monotone FP32 map) and keeps per bucket the
+// best compared coordinate (top 32 key bits); the prefix minimum over lower
+// buckets, seeded with the region's first extreme, gives for every bucket a
+// value such that any region point of that bucket with a larger value is
+// dominated by a sample point of a strictly lower bucket.
 #include "cch_internal.cuh"
 
 namespace cch {
 
+template <int DT>
+struct PointT;
+template <>
+struct PointT<DT_F64> { using T = double2; };
+template <>
+struct PointT<DT_I32> { using T = int2; };
+
+// ------------------------------------------------------------- keys
+
+// Order-preserving key of a float64 as 32-bit words (-0.0 -> +0.0).  Also
+// folds the magnitude of a nonzero value into `amin` (top word), for the
+// lower end of the domain check.
+__device__ __forceinline__ void f64_key_words(uint64_t b, uint32_t& kh, uint32_t& kl, uint32_t& amin) {
+  uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
+  uint32_t a = h & 0x7FFFFFFFu;
+  bool nz = (a | l) != 0;
+  amin = min(amin, nz ? a : 0x7FFFFFFFu);
+  h = nz ? h : 0u;
+  uint32_t m = (uint32_t)((int32_t)h >> 31);
+  kh = h ^ (m | 0x80000000u);
+  kl = l ^ m;
+}
+
+// Top key word only (no domain bookkeeping).
+__device__ __forceinline__ uint32_t f64_key_hi(uint64_t b) {
+  uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
+  if (((h & 0x7FFFFFFFu) | l) == 0) h = 0;
+  return h ^ ((uint32_t)((int32_t)h >> 31) | 0x80000000u);
+}
+
+__device__ __forceinline__ uint64_t kw(uint32_t h, uint32_t l) { return ((uint64_t)h << 32) | l; }
+
 // ------------------------------------------------------------------ a1
 
 // Lexicographic minimum over (k1, k2, idx).  All four extremes are minima:
-// E1 (kx, ky), E2 (ky, kx), E3 (~kx, ~ky), E4 (~ky, ~kx).
+// E1 (kx, ky), E2 (ky, kx), E3 (~kx, ~ky), E4 (~ky, ~kx); int32 packs both
+// 32-bit keys into k1.
 struct Lex {
   uint64_t k1, k2;
   uint32_t idx;
 };
 
-__device__ __forceinline__ bool lex_less(uint64_t a1, uint64_t a2, uint32_t ai,
-                                         uint64_t b1, uint64_t b2, uint32_t bi) {
-  return a1 < b1 || (a1 == b1 && (a2 < b2 || (a2 == b2 && ai < bi)));
+__device__ __forceinline__ bool lex_less(const Lex& a, const Lex& b) {
+  return a.k1 < b.k1 || (a.k1 == b.k1 && (a.k2 < b.k2 || (a.k2 == b.k2 && a.idx < b.idx)));
 }
-
 __device__ __forceinline__ void lex_min_into(Lex& a, const Lex& b) {
-  if (lex_less(b.k1, b.k2, b.idx, a.k1, a.k2, a.idx)) a = b;
+  if (lex_less(b, a)) a = b;
 }
-
 __device__ __forceinline__ Lex lex_shfl(const Lex& v, int o) {
   Lex r;
   r.k1 = __shfl_xor_sync(0xFFFFFFFFu, v.k1, o);
@@ -40,57 +85,141 @@ __device__ __forceinline__ Lex lex_shfl(const Lex& v, int o) {
 }
 
 template <int DT>
-struct PointT;
-template <>
-struct PointT<DT_F64> { using T = double2; };
-template <>
-struct PointT<DT_I32> { using T = int2; };
-
-// Keys of one point.  int32: the 32-bit keys of x and y are packed into k1
-// (so one 64-bit compare orders (x, y)), k2 = 0.
-template <int DT>
-__device__ __forceinline__ void point_keys(const typename PointT<DT>::T& p, uint64_t kk[4][2],
-                                           uint32_t& bad) {
+__device__ __forceinline__ void cand_keys(uint32_t xh, uint32_t xl, uint32_t yh, uint32_t yl, int e,
+                                          uint64_t& k1, uint64_t& k2) {
   if constexpr (DT == DT_F64) {
-    uint64_t bx = (uint64_t)__double_as_longlong(p.x), by = (uint64_t)__double_as_longlong(p.y);
-    bad |= f64_bad(bx) | f64_bad(by);
-    uint64_t kx = key_f64(bx), ky = key_f64(by);
-    kk[0][0] = kx;  kk[0][1] = ky;
-    kk[1][0] = ky;  kk[1][1] = kx;
-    kk[2][0] = ~kx; kk[2][1] = ~ky;
-    kk[3][0] = ~ky; kk[3][1] = ~kx;
+    uint64_t kx = kw(xh, xl), ky = kw(yh, yl);
+    switch (e) {
+      case 0: k1 = kx; k2 = ky; break;
+      case 1: k1 = ky; k2 = kx; break;
+      case 2: k1 = ~kx; k2 = ~ky; break;
+      default: k1 = ~ky; k2 = ~kx; break;
+    }
   } else {
-    uint64_t kx = key_i32(p.x), ky = key_i32(p.y);
-    uint64_t nx = kx ^ 0xFFFFFFFFull, ny = ky ^ 0xFFFFFFFFull;
-    kk[0][0] = (kx << 32) | ky; kk[0][1] = 0;
-    kk[1][0] = (ky << 32) | kx; kk[1][1] = 0;
-    kk[2][0] = (nx << 32) | ny; kk[2][1] = 0;
-    kk[3][0] = (ny << 32) | nx; kk[3][1] = 0;
+    switch (e) {
+      case 0: k1 = kw(xh, yh); break;
+      case 1: k1 = kw(yh, xh); break;
+      case 2: k1 = kw(~xh, ~yh); break;
+      default: k1 = kw(~yh, ~xh); break;
+    }
+    k2 = 0;
+  }
+}
+
+// Fast-path compare: only the top 32 bits of k1 ... everything else in the
+// rare slow path (strict order: indices grow within a thread).
+template <int DT>
+__device__ __forceinline__ void a1_point(const typename PointT<DT>::T& p, uint32_t i, Lex best[4],
+                                         uint32_t th[4], uint32_t& amin) {
+  uint32_t xh, xl, yh, yl;
+  if constexpr (DT == DT_F64) {
+    f64_key_words((uint64_t)__double_as_longlong(p.x), xh, xl, amin);
+    f64_key_words((uint64_t)__double_as_longlong(p.y), yh, yl, amin);
+  } else {
+    xh = (uint32_t)p.x ^ 0x80000000u;
+    yh = (uint32_t)p.y ^ 0x80000000u;
+    xl = yl = 0;
+  }
+  if (xh <= th[0] || yh <= th[1] || ~xh <= th[2] || ~yh <= th[3]) {
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      Lex c;
+      cand_keys<DT>(xh, xl, yh, yl, e, c.k1, c.k2);
+      if (c.k1 < best[e].k1 || (c.k1 == best[e].k1 && c.k2 < best[e].k2)) {
+        best[e].k1 = c.k1;
+        best[e].k2 = c.k2;
+        best[e].idx = i;
+        th[e] = (uint32_t)(c.k1 >> 32);
+      }
+    }
+  }
+}
+
+// Bucket of the stairs map: monotone non-decreasing in u.
+__device__ __forceinline__ int stair_bucket(float u, float lo, float scale) {
+  float t = __fmul_rn(__fsub_rn(u, lo), scale);
+  int b = __float2int_rd(t);
+  return min(max(b, 0), kStairB - 1);
+}
+
+// FP32 view of a point used by the filter and the stairs (truncated float64,
+// rounded int32): monotone in each coordinate.
+template <int DT>
+__device__ __forceinline__ void f32_view(const typename PointT<DT>::T& p, float& X, float& Y) {
+  if constexpr (DT == DT_F64) {
+    X = f64_trunc_f32((uint64_t)__double_as_longlong(p.x));
+    Y = f64_trunc_f32((uint64_t)__double_as_longlong(p.y));
+  } else {
+    X = __int2float_rn(p.x);
+    Y = __int2float_rn(p.y);
+  }
+}
+
+// Compared-coordinate key (top word) of region r (0..3) in "smaller is
+// better" form: R1 y, R2 -x, R3 -y, R4 x.
+template <int DT>
+__device__ __forceinline__ uint32_t cmp_key_hi(const typename PointT<DT>::T& p, int r) {
+  uint32_t xh, yh;
+  if constexpr (DT == DT_F64) {
+    xh = f64_key_hi((uint64_t)__double_as_longlong(p.x));
+    yh = f64_key_hi((uint64_t)__double_as_longlong(p.y));
+  } else {
+    xh = (uint32_t)p.x ^ 0x80000000u;
+    yh = (uint32_t)p.y ^ 0x80000000u;
+  }
+  switch (r) {
+    case 0: return yh;
+    case 1: return ~xh;
+    case 2: return ~yh;
+    default: return xh;
+  }
+}
+
+// Sort coordinate (FP32 view) of region r: R1 x asc, R2 y asc, R3 x desc, R4 y desc.
+__device__ __forceinline__ float sort_u(float X, float Y, int r) {
+  switch (r) {
+    case 0: return X;
+    case 1: return Y;
+    case 2: return -X;
+    default: return -Y;
   }
 }
 
 // Edge set-up of one set, run by one thread once E1..E4 are known.
 template <int DT>
 __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, const Lex best[4],
-                          uint32_t bad) {
+                          uint32_t amin) {
   SetCtl& c = w.ctl[s];
-  if (bad) {
-    c.status = (bad & 1u) ? ST_NONFINITE : ST_RANGE;
-    return;
-  }
   using P = typename PointT<DT>::T;
   const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
   uint32_t flags = 0;
+  P e[4];
   for (int k = 0; k < 4; k++) {
     c.ek1[k] = best[k].k1;
     c.ek2[k] = best[k].k2;
     c.eidx[k] = best[k].idx;
-    P p = pts[best[k].idx];
-    c.ex[k] = (double)p.x;
-    c.ey[k] = (double)p.y;
+    e[k] = pts[best[k].idx];
+    c.ex[k] = (double)e[k].x;
+    c.ey[k] = (double)e[k].y;
+  }
+  if constexpr (DT == DT_F64) {
+    // NaN, Inf and huge values sort beyond every finite value, so they show
+    // up among the extremes; tiny nonzero values were folded into amin.
+    int st = 0;
+    for (int k = 0; k < 4; k++) {
+      for (int q = 0; q < 2; q++) {
+        uint64_t b = (uint64_t)__double_as_longlong(q ? e[k].y : e[k].x);
+        uint32_t ex = (uint32_t)(b >> 52) & 0x7FFu;
+        if (ex == 0x7FFu) st = ST_NONFINITE;
+        else if (ex > 1023u + 399u && st == 0) st = ST_RANGE;
+      }
+    }
+    if (st == 0 && amin < ((1023u - 400u) << 20)) st = ST_RANGE;
+    if (st) { c.status = st; return; }
   }
   for (int k = 0; k < 4; k++)
     if (c.eidx[k] == c.eidx[(k + 1) & 3]) flags |= SF_DEGEN0 << k;
+  bool small = true;
   if constexpr (DT == DT_I32) {
     // E1 = P_minx, E3 = P_maxx, E2 = P_miny, E4 = P_maxy
     double spanx = c.ex[2] - c.ex[0], spany = c.ey[3] - c.ey[1];
@@ -99,16 +228,24 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
     double xm = fmax(fabs(c.ex[0]), fabs(c.ex[2]));
     double ym = fmax(fabs(c.ey[1]), fabs(c.ey[3]));
     const double lim = 1152921504606846976.0;  // 2^60
-    if (xm <= lim && ym <= lim && !(j.opts & OPT_NO_FILTER)) {
-      flags |= SF_FILTER;
-      // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
-      // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on
-      // significand-truncated X, Y differs from the exact value by at most
-      // 5.01 u (|A| Ymax + |B| Xmax + |B||ax| + |A||ay|) plus underflow
-      // terms, u = 2^-24; E below uses 6 u and rounds up.
-      const double u = 5.9604644775390625e-08;
-      for (int k = 0; k < 4; k++) {
-        int k1 = (k + 1) & 3;
+    small = xm <= lim && ym <= lim;
+    const bool filt = small && !(j.opts & OPT_NO_FILTER);
+    if (filt) flags |= SF_FILTER;
+    // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
+    // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on
+    // significand-truncated X, Y differs from the exact value by at most
+    // 5.01 u (|A| Ymax + |B| Xmax + |B||ax| + |A||ay|) plus underflow terms,
+    // u = 2^-24; E below uses 6 u and rounds up.  Without the filter every
+    // point takes the exact path (E = inf); a degenerate edge is always
+    // "inside" (A = B = 0, C = 1, E = 0).
+    const double u = 5.9604644775390625e-08;
+    for (int k = 0; k < 4; k++) {
+      int k1 = (k + 1) & 3;
+      if (!filt) {
+        c.fA[k] = 0.f; c.fB[k] = 0.f; c.fC[k] = 0.f; c.fE[k] = __int_as_float(0x7F800000);
+      } else if (flags & (SF_DEGEN0 << k)) {
+        c.fA[k] = 0.f; c.fB[k] = 0.f; c.fC[k] = 1.f; c.fE[k] = 0.f;
+      } else {
         double ax = c.ex[k], ay = c.ey[k], bx = c.ex[k1], by = c.ey[k1];
         double A = bx - ax, B = by - ay;
         double C = B * ax - A * ay;
@@ -123,6 +260,19 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
       }
     }
   }
+  if (small && !(j.opts & OPT_NO_PREFILTER)) {
+    flags |= SF_STAIRS;
+    float X[4], Y[4];
+    for (int k = 0; k < 4; k++) f32_view<DT>(e[k], X[k], Y[k]);
+    // region r runs from E_r to E_{r+1} along its sort coordinate
+    for (int r = 0; r < 4; r++) {
+      int r1 = (r + 1) & 3;
+      float lo = sort_u(X[r], Y[r], r), hi = sort_u(X[r1], Y[r1], r);
+      c.slo[r] = lo;
+      c.shi[r] = hi;
+      c.sscale[r] = hi > lo ? (float)kStairB / (hi - lo) : 0.f;
+    }
+  }
   c.flags = flags;
 }
 
@@ -130,7 +280,7 @@ template <int DT>
 __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
   using P = typename PointT<DT>::T;
   __shared__ Lex red[kWarps][4];
-  __shared__ uint32_t red_bad[kWarps];
+  __shared__ uint32_t red_amin[kWarps];
   __shared__ int last;
 
   const int chunk = blockIdx.x;
@@ -149,9 +299,10 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
   const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
 
   Lex best[4];
+  uint32_t th[4];
 #pragma unroll
-  for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
-  uint32_t bad = 0;
+  for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; th[k] = 0xFFFFFFFFu; }
+  uint32_t amin = 0x7FFFFFFFu;
 
   constexpr int U = 4;
   for (int64_t base = c0; base < c1; base += (int64_t)kThreads * U) {
@@ -164,17 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
 #pragma unroll
     for (int u = 0; u < U; u++) {
       int64_t i = base + u * kThreads + threadIdx.x;
-      if (i < c1) {
-        uint64_t kk[4][2];
-        point_keys<DT>(v[u], kk, bad);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          // indices grow within a thread: strict order keeps the smallest
-          if (kk[k][0] < best[k].k1 || (kk[k][0] == best[k].k1 && kk[k][1] < best[k].k2)) {
-            best[k].k1 = kk[k][0]; best[k].k2 = kk[k][1]; best[k].idx = (uint32_t)i;
-          }
-        }
-      }
+      if (i < c1) a1_point<DT>(v[u], (uint32_t)i, best, th, amin);
     }
   }
 
@@ -183,64 +324,163 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
-    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+    amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
-    red_bad[warp] = bad;
+    red_amin[warp] = amin;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 1; q < kWarps; q++) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
-      bad |= red_bad[q];
+      amin = min(amin, red_amin[q]);
     }
     Part& pt = w.part[chunk];
     for (int k = 0; k < 4; k++) { pt.k1[k] = best[k].k1; pt.k2[k] = best[k].k2; pt.idx[k] = best[k].idx; }
-    pt.bad = bad;
+    pt.bad = amin;
     __threadfence();
     last = atomicAdd(&w.ctl[s].arrive1, 1u) == (uint32_t)(sd.nchunk1 - 1);
   }
   __syncthreads();
   if (!last) return;
 
-  // Last chunk of the set: reduce the set's partials, clear its histogram
-  // (accumulated by the sort later), set up its edges.
+  // Last chunk of the set: reduce the set's partials, clear its sort
+  // histogram and stairs table, set up its edges.
   __threadfence();
   uint32_t* hist = w.hist + (size_t)s * kSortPasses * 256;
   for (int i = threadIdx.x; i < kSortPasses * 256; i += kThreads) hist[i] = 0;
+  uint32_t* stt = w.stairs + (size_t)s * 4 * kStairB;
+  for (int i = threadIdx.x; i < 4 * kStairB; i += kThreads) stt[i] = 0xFFFFFFFFu;
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
-  bad = 0;
+  amin = 0x7FFFFFFFu;
   for (int q = threadIdx.x; q < sd.nchunk1; q += kThreads) {
     const Part& pt = w.part[sd.chunk1 + q];
     for (int k = 0; k < 4; k++) {
       Lex v{pt.k1[k], pt.k2[k], pt.idx[k]};
       lex_min_into(best[k], v);
     }
-    bad |= pt.bad;
+    amin = min(amin, pt.bad);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
-    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+    amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
   }
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
-    red_bad[warp] = bad;
+    red_amin[warp] = amin;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 1; q < kWarps; q++) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
-      bad |= red_bad[q];
+      amin = min(amin, red_amin[q]);
     }
-    setup_set<DT>(j, w, s, sd, best, bad);
+    setup_set<DT>(j, w, s, sd, best, amin);
+  }
+}
+
+// ------------------------------------------------------------ stairs
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
+  using P = typename PointT<DT>::T;
+  __shared__ uint32_t tb[4][kStairB];
+  __shared__ int last;
+  const int chunk = blockIdx.x;
+  int s = 0;
+  if (j.sets) {
+    int lo = 0, hi = j.nsets - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (j.sets[mid].chunk3 <= chunk) lo = mid; else hi = mid - 1;
+    }
+    s = lo;
+  }
+  const SetDesc sd = get_set(j, s);
+  const SetCtl& c = w.ctl[s];
+  if (c.status != 0 || !(c.flags & SF_STAIRS)) return;   // uniform; table unused
+  float lo[4], hi[4], sc[4];
+#pragma unroll
+  for (int r = 0; r < 4; r++) { lo[r] = c.slo[r]; hi[r] = c.shi[r]; sc[r] = c.sscale[r]; }
+  for (int i = threadIdx.x; i < 4 * kStairB; i += kThreads) (&tb[0][0])[i] = 0xFFFFFFFFu;
+  __syncthreads();
+
+  const int64_t m = stairs_sample(sd.n);
+  const int64_t c0 = sd.n - m + (int64_t)(chunk - sd.chunk3) * kStairChunk;
+  const int64_t c1 = min(sd.n, c0 + kStairChunk);
+  const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
+  constexpr int U = 8;
+  for (int64_t b0 = c0; b0 < c1; b0 += (int64_t)kThreads * U) {
+    P v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      int64_t i = b0 + u * kThreads + threadIdx.x;
+      if (i < c1) v[u] = pts[i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      int64_t i = b0 + u * kThreads + threadIdx.x;
+      if (i >= c1) continue;
+      float X, Y;
+      f32_view<DT>(v[u], X, Y);
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        float su = sort_u(X, Y, r);
+        if (su >= lo[r] && su <= hi[r])
+          atomicMin(&tb[r][stair_bucket(su, lo[r], sc[r])], cmp_key_hi<DT>(v[u], r));
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t* g = w.stairs + (size_t)s * 4 * kStairB;
+  for (int i = threadIdx.x; i < 4 * kStairB; i += kThreads) {
+    uint32_t v = (&tb[0][0])[i];
+    if (v != 0xFFFFFFFFu) atomicMin(g + i, v);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&w.ctl[s].arrive3, 1u) == (uint32_t)(sd.nchunk3 - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // exclusive prefix minimum per region, seeded with the first extreme
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 4) {
+    const int r = warp;
+    P e;
+    if constexpr (DT == DT_F64) { e.x = c.ex[r]; e.y = c.ey[r]; }
+    else { e.x = (int)c.ex[r]; e.y = (int)c.ey[r]; }
+    uint32_t run = cmp_key_hi<DT>(e, r);
+    uint32_t* t = g + r * kStairB;
+    constexpr int per = kStairB / 32;
+    uint32_t loc[per];
+    uint32_t mn = 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < per; q++) { loc[q] = *(volatile uint32_t*)(t + lane * per + q); mn = min(mn, loc[q]); }
+    uint32_t x = mn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x = min(x, y);
+    }
+    uint32_t ex = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+    if (lane == 0) ex = 0xFFFFFFFFu;
+    ex = min(ex, run);
+#pragma unroll
+    for (int q = 0; q < per; q++) {
+      t[lane * per + q] = ex;
+      ex = min(ex, loc[q]);
+    }
   }
 }
 
@@ -256,7 +496,7 @@ __device__ void plan_sort(const Job& j, const Ws& w) {
   for (int base = 0; base < j.nsets; base += kThreads) {
     int s = base + threadIdx.x;
     uint32_t t = 0;
-    if (s < j.nsets) t = (w.ctl[s].s1 + kSortTile - 1) / kSortTile;
+    if (s < j.nsets && (w.ctl[s].flags & SF_BIG)) t = (w.ctl[s].s1 + kSortTile - 1) / kSortTile;
     uint32_t x = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -278,53 +518,31 @@ __device__ void plan_sort(const Job& j, const Ws& w) {
   }
 }
 
-// Region of one point: 1..4, or 0 inside / on the quadrilateral.
-template <int DT>
-struct EdgeCache {
-  float fA[4], fB[4], fC[4], fE[4];
-  double ex[4], ey[4];
-  int ix[4], iy[4];
-  uint32_t flags;
-};
-
-template <int DT>
-__device__ __forceinline__ int region_of(const EdgeCache<DT>& e, const typename PointT<DT>::T& p) {
-  if constexpr (DT == DT_F64) {
-    if (e.flags & SF_FILTER) {
-      uint64_t bx = (uint64_t)__double_as_longlong(p.x), by = (uint64_t)__double_as_longlong(p.y);
-      float X = f64_trunc_f32(bx), Y = f64_trunc_f32(by);
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        if (e.flags & (SF_DEGEN0 << k)) continue;
-        float d = __fmaf_rn(e.fA[k], Y, __fmaf_rn(-e.fB[k], X, e.fC[k]));
-        if (d > e.fE[k]) continue;             // certainly left of (inside) edge k
-        if (d < -e.fE[k]) return k + 1;        // certainly right (outside)
-        int k1 = (k + 1) & 3;
-        if (orient_f64(e.ex[k], e.ey[k], e.ex[k1], e.ey[k1], p.x, p.y) < 0) return k + 1;
-      }
-      return 0;
-    }
-#pragma unroll 1
-    for (int k = 0; k < 4; k++) {
-      if (e.flags & (SF_DEGEN0 << k)) continue;
-      int k1 = (k + 1) & 3;
-      if (orient_f64(e.ex[k], e.ey[k], e.ex[k1], e.ey[k1], p.x, p.y) < 0) return k + 1;
-    }
-    return 0;
-  } else {
-    const bool wide = (e.flags & SF_WIDE) != 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      if (e.flags & (SF_DEGEN0 << k)) continue;
-      int k1 = (k + 1) & 3;
-      if (orient_i32(e.ix[k], e.iy[k], e.ix[k1], e.iy[k1], p.x, p.y, wide) < 0) return k + 1;
-    }
-    return 0;
+// Exact region test of one point (every edge: FP64 filter, then expansion
+// arithmetic).  Kept out of line: only points the FP32 filter cannot decide
+// get here.
+__device__ __noinline__ int region_exact_f64(double px, double py, const double* ex, const double* ey,
+                                             uint32_t flags) {
+  for (int k = 0; k < 4; k++) {
+    if (flags & (SF_DEGEN0 << k)) continue;
+    int k1 = (k + 1) & 3;
+    if (orient_f64(ex[k], ey[k], ex[k1], ey[k1], px, py) < 0) return k + 1;
   }
+  return 0;
 }
 
-// Table 1 sort key of a region-r point: R1 x asc, R2 y asc, R3 x desc,
-// R4 y desc (ascending order of the returned key).
+__device__ __noinline__ int region_exact_i32_wide(int px, int py, const int* ix, const int* iy,
+                                                  uint32_t flags) {
+  for (int k = 0; k < 4; k++) {
+    if (flags & (SF_DEGEN0 << k)) continue;
+    int k1 = (k + 1) & 3;
+    if (orient_i32(ix[k], iy[k], ix[k1], iy[k1], px, py, true) < 0) return k + 1;
+  }
+  return 0;
+}
+
+// Table 1 sort key of a region-r point (r = 1..4): R1 x asc, R2 y asc,
+// R3 x desc, R4 y desc, as an ascending order-preserving integer key.
 template <int DT>
 __device__ __forceinline__ uint64_t sort_key(const typename PointT<DT>::T& p, int r) {
   uint64_t kx, ky, m;
@@ -346,80 +564,178 @@ __device__ __forceinline__ uint64_t sort_key(const typename PointT<DT>::T& p, in
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kThreads) k_classify(Job j, Ws w) {
+constexpr int cls_smem_bytes() {
+  return kClsStages * (kClsTileBytes + 16);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
   using P = typename PointT<DT>::T;
-  __shared__ int sh_tile;
-  __shared__ int sh_set;
-  __shared__ EdgeCache<DT> ec;
-  __shared__ int32_t sh_status;
-  __shared__ uint32_t cnt[kClsItems][kWarps];
-  __shared__ uint32_t sh_excl, sh_agg;
-  __shared__ int sh_last;
+  constexpr int PB = (int)sizeof(P);
+  constexpr int TILE = kClsTileBytes / PB;
+  constexpr int ITEMS = TILE / kThreads;
+  constexpr int SB = kClsTileBytes + 16;        // stage bytes (16 bytes of slack in front)
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[kClsStages];
+  __shared__ int st_tile[kClsStages], st_set[kClsStages], st_head[kClsStages];
+  __shared__ uint32_t cnt[ITEMS][kWarps];
+  __shared__ uint32_t bal[ITEMS][kWarps];
+  __shared__ uint32_t rcnt[4];
+  __shared__ int sh_set, sh_status;
+  __shared__ uint32_t sh_flags;
+  __shared__ float sh_f[4][4];
+  __shared__ float sh_st[3][4];
+  __shared__ double sh_ex[4], sh_ey[4];
+  __shared__ int sh_ix[4], sh_iy[4];
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t tag = j.epoch << 4;   // pass field 0
-  if (threadIdx.x == 0) sh_set = -1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (;;) {
-    if (threadIdx.x == 0) sh_tile = (int)atomicAdd(w.ctr + CT_CLS_TILE, 1u);
-    __syncthreads();
-    const int tile = sh_tile;
-    if (tile >= j.ntile2) break;
+  // producer: acquire the next tile and start its copy into `slot`
+  auto issue = [&](int slot) {
+    const uint32_t t = atomicAdd(w.ctr + CT_CLS_TILE, 1u);
+    st_tile[slot] = (int)t;
+    if (t >= (uint32_t)j.ntile2) return;
     int s = 0;
     if (j.sets) {
       int lo = 0, hi = j.nsets - 1;
       while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (j.sets[mid].tile2 <= tile) lo = mid; else hi = mid - 1;
+        if (j.sets[mid].tile2 <= (int)t) lo = mid; else hi = mid - 1;
       }
       s = lo;
     }
+    st_set[slot] = s;
     const SetDesc sd = get_set(j, s);
-    if (s != sh_set) {
+    const int64_t i0 = (int64_t)(t - sd.tile2) * TILE;
+    const int np = (int)min((int64_t)TILE, sd.n - i0);
+    const char* src = reinterpret_cast<const char*>(j.pts) + (sd.off + i0) * PB;
+    unsigned char* dst = smem + slot * SB + 16;
+    const int head = ((uintptr_t)src & 15) ? 1 : 0;       // int32 only
+    const int rem = np - head;
+    const int tail = ((rem * PB) & 15) ? 1 : 0;
+    const uint32_t bytes = (uint32_t)(rem - tail) * PB;
+    st_head[slot] = head;
+    if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
+    if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
+    mbar_arrive_tx(&bar[slot], bytes);
+    if (bytes) tma_load_1d(dst, src + head * PB, bytes, &bar[slot]);
+  };
+
+  if (tid == 0) {
+    for (int q = 0; q < kClsStages; q++) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+    fence_async_smem();
+    sh_set = -1;
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int q = 0; q < kClsStages; q++) issue(q);
+  __syncthreads();
+
+  float fA[4], fB[4], fC[4], fE[4], slo[4], ssc[4];
+  int ix[4], iy[4];
+  uint32_t flags = 0;
+  bool stairs_on = false;
+
+  for (int it = 0;; it++) {
+    const int slot = it % kClsStages;
+    const uint32_t parity = (uint32_t)(it / kClsStages) & 1u;
+    const int tile = st_tile[slot];
+    if (tile >= j.ntile2) break;
+    const int s = st_set[slot];
+    const SetDesc sd = get_set(j, s);
+    if (s != sh_set) {            // uniform: a new set's parameters
       __syncthreads();
-      if (threadIdx.x == 0) {
+      if (tid == 0) {
         const SetCtl& c = w.ctl[s];
         for (int k = 0; k < 4; k++) {
-          ec.fA[k] = c.fA[k]; ec.fB[k] = c.fB[k]; ec.fC[k] = c.fC[k]; ec.fE[k] = c.fE[k];
-          ec.ex[k] = c.ex[k]; ec.ey[k] = c.ey[k];
-          ec.ix[k] = (int)c.ex[k]; ec.iy[k] = (int)c.ey[k];
+          sh_f[0][k] = c.fA[k]; sh_f[1][k] = -c.fB[k]; sh_f[2][k] = c.fC[k]; sh_f[3][k] = c.fE[k];
+          sh_st[0][k] = c.slo[k]; sh_st[1][k] = c.sscale[k];
+          sh_ex[k] = c.ex[k]; sh_ey[k] = c.ey[k];
+          sh_ix[k] = (int)c.ex[k]; sh_iy[k] = (int)c.ey[k];
         }
-        ec.flags = c.flags;
+        sh_flags = c.flags;
         sh_status = c.status;
         sh_set = s;
       }
       __syncthreads();
-    }
-    if (sh_status != 0) { __syncthreads(); continue; }   // whole set skipped
-
-    const int64_t lt = tile - sd.tile2;
-    const int64_t t0 = lt * kClsTile;
-    const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
-
-    P v[kClsItems];
 #pragma unroll
-    for (int it = 0; it < kClsItems; it++) {
-      int64_t i = t0 + it * kThreads + threadIdx.x;
-      if (i < sd.n) v[it] = pts[i];
+      for (int k = 0; k < 4; k++) {
+        fA[k] = sh_f[0][k]; fB[k] = sh_f[1][k]; fC[k] = sh_f[2][k]; fE[k] = sh_f[3][k];
+        slo[k] = sh_st[0][k]; ssc[k] = sh_st[1][k];
+        ix[k] = sh_ix[k]; iy[k] = sh_iy[k];
+      }
+      flags = sh_flags;
+      stairs_on = (flags & SF_STAIRS) != 0;
     }
+    // wait for the tile (bounded; a copy always completes unless the device
+    // is failing, in which case the call reports CCH_ERR_TIMEOUT)
+    {
+      uint32_t spins = 0;
+      bool ok = true;
+      while (!mbar_try_wait(&bar[slot], parity)) {
+        if (!spin_step(spins, w.ctr)) { ok = false; break; }
+      }
+      if (!ok) { __syncthreads(); break; }
+    }
+    const int64_t lt = tile - sd.tile2;
+    const int64_t t0 = lt * TILE;
+    const int np = (int)min((int64_t)TILE, sd.n - t0);
+    const unsigned char* base = smem + slot * SB + 16 - st_head[slot] * PB;
+    const bool skip_set = sh_status != 0;
+    const uint32_t* pre = w.stairs + (size_t)s * 4 * kStairB;
+
     uint64_t regs = 0;    // 4 bits per item
 #pragma unroll
-    for (int it = 0; it < kClsItems; it++) {
-      int64_t i = t0 + it * kThreads + threadIdx.x;
+    for (int k = 0; k < ITEMS; k++) {
+      const int i = k * kThreads + tid;
       int r = 0;
-      if (i < sd.n) r = region_of<DT>(ec, v[it]);
-      regs |= (uint64_t)r << (4 * it);
-      uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
-      if (lane == 0) cnt[it][warp] = __popc(b);
+      if (i < np && !skip_set) {
+        const P p = *reinterpret_cast<const P*>(base + (size_t)i * PB);
+        float X, Y;
+        f32_view<DT>(p, X, Y);
+        if constexpr (DT == DT_F64) {
+          float d0 = __fmaf_rn(fA[0], Y, __fmaf_rn(fB[0], X, fC[0]));
+          float d1 = __fmaf_rn(fA[1], Y, __fmaf_rn(fB[1], X, fC[1]));
+          float d2 = __fmaf_rn(fA[2], Y, __fmaf_rn(fB[2], X, fC[2]));
+          float d3 = __fmaf_rn(fA[3], Y, __fmaf_rn(fB[3], X, fC[3]));
+          r = d0 < -fE[0] ? 1 : !(d0 > fE[0]) ? -1
+            : d1 < -fE[1] ? 2 : !(d1 > fE[1]) ? -1
+            : d2 < -fE[2] ? 3 : !(d2 > fE[2]) ? -1
+            : d3 < -fE[3] ? 4 : !(d3 > fE[3]) ? -1 : 0;
+          if (r < 0) r = region_exact_f64(p.x, p.y, sh_ex, sh_ey, flags);
+        } else {
+          if (flags & SF_WIDE) {
+            r = region_exact_i32_wide(p.x, p.y, sh_ix, sh_iy, flags);
+          } else {
+#pragma unroll
+            for (int q = 3; q >= 0; q--) {
+              if (!(flags & (SF_DEGEN0 << q)) &&
+                  orient_i32(ix[q], iy[q], ix[(q + 1) & 3], iy[(q + 1) & 3], p.x, p.y, false) < 0)
+                r = q + 1;
+            }
+          }
+        }
+        if (r > 0 && stairs_on) {
+          const int q = r - 1;
+          const int b = stair_bucket(sort_u(X, Y, q), slo[q], ssc[q]);
+          if (cmp_key_hi<DT>(p, q) > __ldg(pre + q * kStairB + b)) r = 0;   // dominated
+        }
+      }
+      regs |= (uint64_t)r << (4 * k);
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
+      if (lane == 0) { cnt[k][warp] = __popc(b); bal[k][warp] = b; }
     }
     __syncthreads();
-    // exclusive scan over (item, warp) in point order
-    if (threadIdx.x < 32) {
-      uint32_t loc[kClsItems * kWarps / 32];
+    // exclusive scan over (item, warp) in point order: positions within the
+    // tile's own slot range; per-region counts of the tile
+    if (warp == 0) {
+      constexpr int per = ITEMS * kWarps / 32;
+      uint32_t loc[per];
       uint32_t sum = 0;
 #pragma unroll
-      for (int q = 0; q < kClsItems * kWarps / 32; q++) {
-        int f = lane * (kClsItems * kWarps / 32) + q;
+      for (int q = 0; q < per; q++) {
+        int f = lane * per + q;
         loc[q] = cnt[f / kWarps][f % kWarps];
         sum += loc[q];
       }
@@ -431,57 +747,173 @@ __global__ void __launch_bounds__(kThreads) k_classify(Job j, Ws w) {
       }
       uint32_t run = x - sum;
 #pragma unroll
-      for (int q = 0; q < kClsItems * kWarps / 32; q++) {
-        int f = lane * (kClsItems * kWarps / 32) + q;
+      for (int q = 0; q < per; q++) {
+        int f = lane * per + q;
         cnt[f / kWarps][f % kWarps] = run;
         run += loc[q];
       }
-      const uint32_t agg = __shfl_sync(0xFFFFFFFFu, x, 31);
-      // decoupled look-back across the tiles of this set
-      uint64_t* st = w.st2;
-      uint32_t excl = 0;
-      if (lt == 0) {
-        if (lane == 0) st_rel_u64(st + tile, lb_pack(tag, 2, agg));
-      } else {
-        if (lane == 0) st_rel_u64(st + tile, lb_pack(tag, 1, agg));
-        excl = lookback_sum(st, tile, sd.tile2, tag, w.ctr);
-        if (lane == 0) st_rel_u64(st + tile, lb_pack(tag, 2, excl + agg));
-      }
-      if (lane == 0) {
-        sh_excl = excl;
-        sh_agg = agg;
-        if (lt == sd.ntile2 - 1) w.ctl[s].s1 = excl + agg;
-      }
+      if (lane < 4) rcnt[lane] = 0;
     }
     __syncthreads();
-    const uint32_t excl = sh_excl;
-    uint64_t* keys = w.keyA + sd.off;
-    uint32_t* vals = w.valA + sd.off;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    if (regs) {
+      uint64_t* keys = w.keyB + sd.off + t0;
+      uint32_t* vals = w.valB + sd.off + t0;
+      const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-    for (int it = 0; it < kClsItems; it++) {
-      int r = (int)((regs >> (4 * it)) & 0xF);
-      uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
-      if (r != 0) {
-        uint32_t pos = excl + cnt[it][warp] + __popc(b & lt_mask);
-        int64_t i = t0 + it * kThreads + threadIdx.x;
-        keys[pos] = sort_key<DT>(v[it], r);
-        vals[pos] = ((uint32_t)(r - 1) << 30) | (uint32_t)i;
+      for (int k = 0; k < ITEMS; k++) {
+        const int r = (int)((regs >> (4 * k)) & 0xF);
+        if (r != 0) {
+          const uint32_t b = bal[k][warp];
+          const int i = k * kThreads + tid;
+          const P p = *reinterpret_cast<const P*>(base + (size_t)i * PB);
+          const uint32_t pos = cnt[k][warp] + __popc(b & lt_mask);
+          keys[pos] = sort_key<DT>(p, r);
+          vals[pos] = ((uint32_t)(r - 1) << 30) | (uint32_t)(t0 + i);
+          atomicAdd(&rcnt[r - 1], 1u);
+        }
       }
+    }
+    __syncthreads();                     // slot and st_tile[slot] free again
+    if (tid == 0) {
+      w.tcnt[tile] = (uint64_t)rcnt[0] | ((uint64_t)rcnt[1] << 16) | ((uint64_t)rcnt[2] << 32) |
+                     ((uint64_t)rcnt[3] << 48);
+      fence_async_smem();
+      issue(slot);
+    }
+  }
+}
+
+// ------------------------------------------------------------ gather plan
+//
+// After a2 every tile holds its survivors (index order, regions mixed) at the
+// start of its own slot range, and its per-region counts in tcnt.  k_plan
+// gives every tile its per-region exclusive offset within the set (toff) and
+// every set its region totals; its last CTA decides per set between the
+// shared-memory path (all regions <= kSmallMax) and the multi-CTA sort, and
+// plans both.  k_gather then moves the records into region-major order.
+
+__global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
+  __shared__ uint32_t wsum[4][kWarps];
+  __shared__ uint32_t carry[4];
+  __shared__ int sh_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int s = blockIdx.x; s < j.nsets; s += gridDim.x) {
+    const SetDesc sd = get_set(j, s);
+    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < sd.ntile2; b0 += kThreads) {
+      const int t = b0 + threadIdx.x;
+      uint64_t c = t < sd.ntile2 ? w.tcnt[sd.tile2 + t] : 0ull;
+      uint32_t v[4], x[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) { v[r] = (uint32_t)(c >> (16 * r)) & 0xFFFFu; x[r] = v[r]; }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[r], o);
+          if (lane >= o) x[r] += y;
+        }
+      }
+      if (lane == 31)
+        for (int r = 0; r < 4; r++) wsum[r][warp] = x[r];
+      __syncthreads();
+      uint32_t pre[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        pre[r] = carry[r];
+        for (int q = 0; q < warp; q++) pre[r] += wsum[r][q];
+      }
+      if (t < sd.ntile2)
+        w.toff[sd.tile2 + t] = make_uint4(pre[0] + x[0] - v[0], pre[1] + x[1] - v[1],
+                                          pre[2] + x[2] - v[2], pre[3] + x[3] - v[3]);
+      __syncthreads();
+      if (threadIdx.x == kThreads - 1)
+        for (int r = 0; r < 4; r++) carry[r] = pre[r] + x[r];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      SetCtl& c = w.ctl[s];
+      uint32_t s1 = 0;
+      bool big = false;
+      for (int r = 0; r < 4; r++) {
+        c.cnt[r] = carry[r];
+        s1 += carry[r];
+        big |= carry[r] > (uint32_t)kSmallMax;
+      }
+      c.s1 = s1;
+      if (big) c.flags |= SF_BIG;
     }
     __syncthreads();
   }
-
-  // last CTA out: plan the sort
+  // last CTA: plan the multi-CTA sort (big sets) and list the small segments
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    sh_last = atomicAdd(w.ctr + CT_CLS_DONE, 1u) == gridDim.x - 1;
+    sh_last = atomicAdd(w.ctr + CT_PLAN_DONE, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (sh_last) {
-    __threadfence();
-    plan_sort(j, w);
+  if (!sh_last) return;
+  __threadfence();
+  plan_sort(j, w);
+  if (threadIdx.x == 0) {
+    uint32_t k = 0;
+    for (int s = 0; s < j.nsets; s++) {
+      const SetCtl& c = w.ctl[s];
+      if (c.status != 0 || (c.flags & SF_BIG)) continue;
+      for (int r = 0; r < 4; r++)
+        if (c.cnt[r]) w.small_seg[k++] = (uint32_t)(4 * s + r);
+    }
+    w.ctr[CT_SMALL_TOTAL] = k;
+  }
+}
+
+// One warp per a2 tile: stable move of the tile's survivors to their
+// region-major positions in the set's record stream.
+__global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int nw = gridDim.x * kWarps;
+  for (int t = blockIdx.x * kWarps + (threadIdx.x >> 5); t < j.ntile2; t += nw) {
+    const uint64_t tc = w.tcnt[t];
+    if (tc == 0) continue;
+    int s = 0;
+    if (j.sets) {
+      int lo = 0, hi = j.nsets - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (j.sets[mid].tile2 <= t) lo = mid; else hi = mid - 1;
+      }
+      s = lo;
+    }
+    const SetDesc sd = get_set(j, s);
+    const SetCtl& c = w.ctl[s];
+    const uint4 of = w.toff[t];
+    uint32_t base[4];
+    base[0] = of.x;
+    base[1] = c.cnt[0] + of.y;
+    base[2] = c.cnt[0] + c.cnt[1] + of.z;
+    base[3] = c.cnt[0] + c.cnt[1] + c.cnt[2] + of.w;
+    const uint32_t n = (uint32_t)(tc & 0xFFFFu) + (uint32_t)((tc >> 16) & 0xFFFFu) +
+                       (uint32_t)((tc >> 32) & 0xFFFFu) + (uint32_t)(tc >> 48);
+    const int64_t src = sd.off + (int64_t)(t - sd.tile2) * cls_tile(j.dtype);
+    for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool ok = i < n;
+      const uint64_t key = ok ? w.keyB[src + i] : 0;
+      const uint32_t val = ok ? w.valB[src + i] : 0;
+      const int r = ok ? (int)(val >> 30) : -1;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, r == q);
+        if (r == q) {
+          const uint32_t pos = base[q] + __popc(b & lt_mask);
+          w.keyA[sd.off + pos] = key;
+          w.valA[sd.off + pos] = val;
+        }
+        base[q] += __popc(b);
+      }
+    }
   }
 }
 
@@ -492,17 +924,49 @@ int extremes_blocks_per_sm(int dtype) {
   return b > 0 ? b : 1;
 }
 
-void launch_extremes(const Job& j, const Ws& w, const Launch& L) {
-  if (j.nchunk1 == 0) return;
+int launch_extremes(const Job& j, const Ws& w, const Launch& L) {
+  if (j.nchunk1 == 0) return 0;
   if (j.dtype == DT_F64) k_extremes<DT_F64><<<j.nchunk1, kThreads, 0, L.stream>>>(j, w);
   else k_extremes<DT_I32><<<j.nchunk1, kThreads, 0, L.stream>>>(j, w);
+  return 1;
 }
 
-void launch_classify(const Job& j, const Ws& w, const Launch& L) {
-  int grid = j.ntile2 < L.grid_cap ? j.ntile2 : L.grid_cap;
+int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
+  if (j.nchunk3 == 0) return 0;
+  if (j.dtype == DT_F64) k_stairs<DT_F64><<<j.nchunk3, kThreads, 0, L.stream>>>(j, w);
+  else k_stairs<DT_I32><<<j.nchunk3, kThreads, 0, L.stream>>>(j, w);
+  return 1;
+}
+
+int launch_gather(const Job& j, const Ws& w, const Launch& L) {
+  int gp = j.nsets < L.grid_cap ? j.nsets : L.grid_cap;
+  k_plan<<<gp < 1 ? 1 : gp, kThreads, 0, L.stream>>>(j, w);
+  int gg = (j.ntile2 + kWarps - 1) / kWarps;
+  if (gg > L.grid_cap) gg = L.grid_cap;
+  if (gg < 1) gg = 1;
+  k_gather<<<gg, kThreads, 0, L.stream>>>(j, w);
+  return 2;
+}
+
+int launch_classify(const Job& j, const Ws& w, const Launch& L) {
+  int grid = j.ntile2 < L.cls_grid ? j.ntile2 : L.cls_grid;
   if (grid < 1) grid = 1;
-  if (j.dtype == DT_F64) k_classify<DT_F64><<<grid, kThreads, 0, L.stream>>>(j, w);
-  else k_classify<DT_I32><<<grid, kThreads, 0, L.stream>>>(j, w);
+  if (j.dtype == DT_F64) {
+    static bool once = [] {
+      cudaFuncSetAttribute(k_classify<DT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT_F64>());
+      return true;
+    }();
+    (void)once;
+    k_classify<DT_F64><<<grid, kThreads, cls_smem_bytes<DT_F64>(), L.stream>>>(j, w);
+  } else {
+    static bool once = [] {
+      cudaFuncSetAttribute(k_classify<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT_I32>());
+      return true;
+    }();
+    (void)once;
+    k_classify<DT_I32><<<grid, kThreads, cls_smem_bytes<DT_I32>(), L.stream>>>(j, w);
+  }
+  return 1;
 }
 
 }  // namespace cch

@@ -36,10 +36,8 @@ __device__ void plan_spa(const Job& j, const Ws& w) {
     int g = base + threadIdx.x;
     uint32_t t = 0;
     if (g < nseg) {
-      int s = g >> 2, r = g & 3;
-      uint32_t c = w.ctl[s].s1 ? w.hist[((size_t)s * kSortPasses + 8) * 256 + r] : 0u;
-      w.ctl[s].cnt[r] = c;
-      t = (c + kSpaTile - 1) / kSpaTile;
+      const SetCtl& c = w.ctl[g >> 2];
+      if (c.flags & SF_BIG) t = (c.cnt[g & 3] + kSpaTile - 1) / kSpaTile;
     }
     uint32_t x = t;
 #pragma unroll
@@ -245,15 +243,18 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(Job j, Ws w, int p) {
   }
 }
 
-void launch_sort(const Job& j, const Ws& w, const Launch& L) {
+int launch_sort(const Job& j, const Ws& w, const Launch& L) {
   int64_t tiles_max = j.N / kSortTile + j.nsets;
   int grid = (int)(tiles_max < L.grid_cap ? tiles_max : L.grid_cap);
   if (grid < 1) grid = 1;
   k_sort_hist<<<grid, kThreads, 0, L.stream>>>(j, w);
+  int n = 1;
   for (int p = 0; p < kSortPasses; p++) {
     if (j.dtype == DT_I32 && p >= 4 && p < 8) continue;   // zero key bytes
     k_sort_pass<<<grid, kThreads, 0, L.stream>>>(j, w, p);
+    n++;
   }
+  return n;
 }
 
 }  // namespace cch

@@ -268,12 +268,13 @@ __global__ void __launch_bounds__(kThreads) k_spa(Job j, Ws w) {
   }
 }
 
-void launch_spa(const Job& j, const Ws& w, const Launch& L) {
+int launch_spa(const Job& j, const Ws& w, const Launch& L) {
   int64_t tiles_max = j.N / kSpaTile + 4 * (int64_t)j.nsets;
   int grid = (int)(tiles_max < L.grid_cap ? tiles_max : L.grid_cap);
   if (grid < 1) grid = 1;
   if (j.dtype == DT_F64) k_spa<DT_F64><<<grid, kThreads, 0, L.stream>>>(j, w);
   else k_spa<DT_I32><<<grid, kThreads, 0, L.stream>>>(j, w);
+  return 1;
 }
 
 }  // namespace cch

@@ -107,23 +107,47 @@ def test_shell_and_far_from_origin():
 
 # ------------------------------------------------------------ stages
 
-@pytest.mark.parametrize("kind", ["square", "disk", "gauss", "i32", "degenerate", "grid"])
+STAGE_KINDS = {
+    "square": lambda n: inputs.square_f64(n, 11),
+    "disk": lambda n: inputs.disk_f64(n, 12),
+    "gauss": lambda n: inputs.gauss_f64(n, 13),
+    "i32": lambda n: inputs.square_i32(n, 14),
+    "idisk": lambda n: inputs.disk_i32(n, 16),
+    "degenerate": lambda n: inputs.degenerate_f64(n, 15),
+    "grid": lambda n: (np.random.default_rng(3).integers(0, 40, (n, 2)) / 8.0),
+    "igrid": lambda n: np.random.default_rng(4).integers(-20, 20, (n, 2)).astype(np.int32),
+}
+
+
+@pytest.mark.parametrize("kind", list(STAGE_KINDS))
 @pytest.mark.parametrize("exact_only", [False, True])
-def test_stage_sets_match_method(kind, exact_only):
+@pytest.mark.parametrize("prefilter", [False, True])
+def test_stage_sets_match_method(kind, exact_only, prefilter):
+    """Round-1 sets (paper mode: no prefilter) and SPA survivors (either
+    mode: the prefilter removes only SPA-dominated points) equal the
+    step-by-step restatement of Sec. 2.1."""
     n = 150_001
-    p = {"square": lambda: inputs.square_f64(n, 11),
-         "disk": lambda: inputs.disk_f64(n, 12),
-         "gauss": lambda: inputs.gauss_f64(n, 13),
-         "i32": lambda: inputs.square_i32(n, 14),
-         "degenerate": lambda: inputs.degenerate_f64(n, 15),
-         "grid": lambda: (np.random.default_rng(3).integers(0, 40, (n, 2)) / 8.0)}[kind]()
-    st = cch.stages(torch.from_numpy(p).to(DEV), exact_only=exact_only)
+    p = STAGE_KINDS[kind](n)
+    st = cch.stages(torch.from_numpy(p).to(DEV), exact_only=exact_only, prefilter=prefilter)
     m = oracle.method(p)
     assert st["status"] == 0
     for r in range(4):
-        assert np.array_equal(st["r1"][r], m["r1"][r]), ("round 1", r)
+        if not prefilter:
+            assert np.array_equal(st["r1"][r], m["r1"][r]), ("round 1", r)
+        else:
+            assert np.isin(st["r1"][r], m["r1"][r]).all(), ("round 1 subset", r)
+            assert np.all(np.diff(st["r1"][r]) > 0)
         assert np.array_equal(st["spa"][r], m["spa"][r]), ("SPA", r)
     assert np.array_equal(st["hull"], m["hull"])
+
+
+def test_prefilter_shrinks_round1_on_uniform_sets():
+    for p in (inputs.square_f64(1_000_000, 5), inputs.disk_f64(1_000_000, 6)):
+        t = torch.from_numpy(p).to(DEV)
+        on = cch.stages(t)
+        off = cch.stages(t, prefilter=False)
+        assert on["counts"][0] * 5 < off["counts"][0]
+        assert np.array_equal(on["hull"], off["hull"])
 
 
 # ------------------------------------------------------------ batched
