@@ -144,6 +144,26 @@ int cch_profile_read(double *stage_ms, int max_stages, int64_t *calls);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 uint64_t cch_launch_count(void);
 
+/*
+ * cch_hull without any device-memory allocation, for callers that cannot
+ * call cudaMalloc: code running under a CUDA graph capture that forbids
+ * allocation, real-time or embedded callers whose device footprint is fixed
+ * at load time, or code running inside an allocator's own callback.  The
+ * paper has no counterpart; this is a property of this library only.
+ *
+ * Arguments, output and errors are those of cch_hull, for at most 131072
+ * points (larger n returns CCH_ERR_RANGE and launches nothing).  Scratch is a
+ * fixed 8 MiB array in the library's device code, held by every GPU that
+ * loads the library until the process exits, and shared by every call on
+ * that GPU: it keeps the previous call's contents (each call clears what must
+ * start at zero), and calls whose work can overlap on the GPU -- different
+ * streams without ordering between them -- race and give wrong results.  The
+ * first call on each device looks up the array's address and clears it; make
+ * that first call before any stream capture.
+ */
+int cch_hull_noalloc(const void *points, int64_t n, int dtype,
+                     int32_t *out_idx, int32_t *out_count, void *stream);
+
 /* Bytes of device scratch one cch_hull call of this size uses. */
 size_t cch_workspace_bytes(int64_t n, int dtype);
 

@@ -51,6 +51,8 @@ def _load():
         lib.cch_hull.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
         lib.cch_hull_batched.restype = ctypes.c_int
         lib.cch_hull_batched.argtypes = [vp, vp, i32, ctypes.c_int, vp, vp, vp]
+        lib.cch_hull_noalloc.restype = ctypes.c_int
+        lib.cch_hull_noalloc.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
         lib.cch_hull_host.restype = ctypes.c_int
         lib.cch_hull_host.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
         lib.cch_hull_stages.restype = ctypes.c_int
