@@ -153,7 +153,7 @@ uint64_t cch_launch_count(void);
  *
  * Arguments, output and errors are those of cch_hull, for at most 131072
  * points (larger n returns CCH_ERR_RANGE and launches nothing).  Scratch is a
- * fixed 8 MiB array in the library's device code, held by every GPU that
+ * fixed 12 MiB array in the library's device code, held by every GPU that
  * loads the library until the process exits, and shared by every call on
  * that GPU: it keeps the previous call's contents (each call clears what must
  * start at zero), and calls whose work can overlap on the GPU -- different

@@ -54,6 +54,7 @@ Layout layout(const Dims& d, char* base) {
   auto take = [&](size_t bytes) { size_t r = o; o = up(o + bytes); return base ? base + r : nullptr; };
   L.w.ctl = (SetCtl*)take(sizeof(SetCtl) * d.nsets);
   L.w.ctr = (uint32_t*)take(sizeof(uint32_t) * CT_COUNT);
+  L.w.ptot = (uint4*)take(16 * ((size_t)d.ntile2 / kPlanTiles + d.nsets + 1));
   L.ctl_bytes = o;
   L.status_off = o;
   L.w.st_sort = (uint64_t*)take(8 * 256 * (size_t)d.max_sort_tiles);
@@ -69,6 +70,8 @@ Layout layout(const Dims& d, char* base) {
   L.w.keyB = (uint64_t*)take(8 * (size_t)d.N);
   L.w.valA = (uint32_t*)take(4 * (size_t)d.N);
   L.w.valB = (uint32_t*)take(4 * (size_t)d.N);
+  L.w.spvA = (uint64_t*)take(8 * (size_t)d.N);
+  L.w.spvB = (uint64_t*)take(8 * (size_t)d.N);
   L.w.hist = (uint32_t*)take(4 * (size_t)kSortPasses * 256 * d.nsets);
   L.w.sort_start = (uint32_t*)take(4 * ((size_t)d.nsets + 1));
   L.w.spa_start = (uint32_t*)take(4 * (4 * (size_t)d.nsets + 1));
@@ -267,8 +270,9 @@ Job single_job(const void* points, int64_t n, int dtype, int32_t* out_idx, int32
   const int ct = cls_tile(dtype);
   j.ntile2 = (int32_t)((n + ct - 1) / ct);
   j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
+  j.nchunkP = (j.ntile2 + kPlanTiles - 1) / kPlanTiles;
   j.sets = nullptr;
-  j.one = SetDesc{0, n, 0, nch, 0, j.ntile2, 0, j.nchunk3};
+  j.one = SetDesc{0, n, 0, nch, 0, j.ntile2, 0, j.nchunk3, 0, j.nchunkP};
   j.out_idx = out_idx;
   j.out_counts = out_count;
   return j;
@@ -318,7 +322,7 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
   std::vector<SetDesc> sets(nsets);
   int target = a1_target(dtype);
   int64_t len = std::max<int64_t>(16384, ((N + target - 1) / std::max(target, 1) + 1023) / 1024 * 1024);
-  int64_t nch = 0, nt = 0, n3 = 0;
+  int64_t nch = 0, nt = 0, n3 = 0, np_ = 0;
   const int ct = cls_tile(dtype);
   for (int32_t s = 0; s < nsets; s++) {
     int64_t n = offsets[s + 1] - offsets[s];
@@ -327,10 +331,12 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
     int32_t c = (int32_t)((n + len - 1) / len);
     int32_t t = (int32_t)((n + ct - 1) / ct);
     int32_t c3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
-    sets[s] = SetDesc{offsets[s], n, (int32_t)nch, c, (int32_t)nt, t, (int32_t)n3, c3};
+    int32_t cp = (t + kPlanTiles - 1) / kPlanTiles;
+    sets[s] = SetDesc{offsets[s], n, (int32_t)nch, c, (int32_t)nt, t, (int32_t)n3, c3, (int32_t)np_, cp};
     nch += c;
     nt += t;
     n3 += c3;
+    np_ += cp;
   }
   Job j{};
   j.pts = points;
@@ -340,6 +346,7 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
   j.nchunk1 = (int32_t)nch;
   j.ntile2 = (int32_t)nt;
   j.nchunk3 = (int32_t)n3;
+  j.nchunkP = (int32_t)np_;
   j.chunk1_len = len;
   j.out_idx = out_idx;
   j.out_counts = out_counts;

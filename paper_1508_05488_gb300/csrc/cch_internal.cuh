@@ -47,6 +47,7 @@ __host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048
 constexpr int kStairB = 1024;          // buckets per region
 constexpr int64_t kStairSample = int64_t(1) << 20;   // sample points per set (the last ones)
 constexpr int kStairChunk = 8192;      // sample points per CTA
+constexpr int kPlanTiles = 1024;       // a2 tiles per gather-plan CTA
 // Sample of a set: its last m points (the most recently streamed by a1),
 // m = min(n, 2^20, max(8192, n / 16)).
 __host__ __device__ inline int64_t stairs_sample(int64_t n) {
@@ -77,6 +78,7 @@ enum : uint32_t {
   SF_WIDE = 2u,         // i32: coordinate spans need 128-bit products
   SF_STAIRS = 4u,       // the dominance prefilter is active for this set
   SF_BIG = 8u,          // some region exceeds kSmallMax survivors: multi-CTA sort
+  SF_SMALL = 256u,      // float64 set with every coordinate below 2^60: FP32 views valid
   SF_DEGEN0 = 16u,      // bit SF_DEGEN0 << k: E_k and E_{k+1} are the same point
 };
 
@@ -106,6 +108,8 @@ struct SetDesc {
   int32_t ntile2;       // a2 tiles of this set
   int32_t chunk3;       // first stairs chunk
   int32_t nchunk3;      // stairs chunks of this set
+  int32_t chunkP;       // first gather-plan chunk (kPlanTiles a2 tiles each)
+  int32_t nchunkP;      // gather-plan chunks of this set
 };
 
 // Per-call launch description.  A single hull carries its descriptor inline;
@@ -118,7 +122,7 @@ struct Job {
   int32_t nchunk1;      // total a1 chunks
   int32_t ntile2;       // total a2 tiles
   int32_t nchunk3;      // total stairs chunks
-  int32_t pad0;
+  int32_t nchunkP;      // total gather-plan chunks
   int64_t chunk1_len;   // a1 chunk length (points), multiple of 256
   uint32_t epoch;       // look-back flag epoch of this call (1..0xFFFF)
   uint32_t opts;        // OPT_* bits
@@ -176,11 +180,13 @@ struct Ws {
   SetCtl* ctl;               // [nsets]
   uint32_t* ctr;             // [CT_COUNT]
   Part* part;                // [nchunk1]
+  uint4* ptot;               // [nchunkP] survivors per region of a gather-plan chunk (cleared per call)
   uint64_t* tcnt;            // [ntile2] survivors of an a2 tile per region (4 x u16)
   uint4* toff;               // [ntile2] exclusive prefix of tcnt over the set's tiles
   uint32_t* small_seg;       // [4 nsets] (set, region) segments of the shared-memory path
   uint64_t* keyA; uint32_t* valA;     // [N] records (sort ping)
   uint64_t* keyB; uint32_t* valB;     // [N] records (sort pong)
+  uint64_t* spvA; uint64_t* spvB;     // [N] SPA value of each record (A: region-major, B: a2 tile slots)
   uint32_t* hist;            // [nsets][kSortPasses][256]
   uint64_t* st_sort;         // [max_sort_tiles][256] look-back words
   uint32_t* sort_start;      // [nsets + 1] first sort tile of each set
@@ -236,15 +242,17 @@ __device__ __forceinline__ uint32_t f64_bad(uint64_t b) {
 }
 
 // float64 -> float32 by truncating the significand (integer ops only; the
-// caller guarantees |v| < 2^100).  |v - t| < 2^-23 |v| for |v| >= 2^-126,
-// t = 0 below that.
+// caller guarantees |v| < 2^100).  The exponent is rebiased by subtracting
+// (1023 - 127) << 20 from the top word, then the top word and the three
+// leading bits of the low word are funnel-shifted into place; magnitudes
+// below 2^-127 become +-0 (2^-127 .. 2^-126 come out as subnormals).  The map
+// is monotone non-decreasing, and |v - t| < 2^-23 |v| for |v| >= 2^-126,
+// |v - t| < 2^-126 below.
 __device__ __forceinline__ float f64_trunc_f32(uint64_t b) {
-  uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-  uint32_t sign = hi & 0x80000000u;
-  int fe = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  uint32_t f = fe <= 0 ? sign : (sign | ((uint32_t)fe << 23) | m);
-  return __uint_as_float(f);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const int t = (int)(hi & 0x7FFFFFFFu) - 0x38000000;
+  const uint32_t sign = hi & 0x80000000u;
+  return __uint_as_float(t < 0 ? sign : (sign | __funnelshift_l(lo, (uint32_t)t, 3)));
 }
 
 // --------------------------------------------------- exact orientation
@@ -331,6 +339,53 @@ __device__ __forceinline__ int orient_f64(double ax, double ay, double bx, doubl
   if (-d > bound) return -1;
   if (l == 0.0 && r == 0.0) return 0;
   return orient_f64_exact_tail(ax, ay, bx, by, cx, cy);
+}
+
+// FP32 filter of orient(a,b,c) for float64 points given their truncated FP32
+// views A, B, C (f64_trunc_f32: |t - v| <= tau |v| + eta, tau = 2^-23,
+// eta = 2^-126).  With the rounded differences u1 = Bx-Ax, v1 = By-Ay,
+// u2 = Cx-Ax, v2 = Cy-Ay, U their largest magnitude, M the largest view
+// magnitude, mu = 2^-24, each difference is within
+//   ed = 2 tau M (1 + 3 tau) + 4 eta + 1.01 mu U
+// of the exact one, and det = fma(u1, v2, -(v1 u2)) is within
+//   E0 = 4 ed U + 2 ed^2 + mu U^2 + mu |det|   (+ 2^-149 for underflow)
+// of the exact determinant (each bound with a (1 + 2 mu) slack).  Returns
+// +1 / -1 when |det| (1 - 2 mu) exceeds 1.01 E0 (the factor covers the
+// rounding of E0 itself), 0 when undecided.  Views outside [2^-60, 2^60] in
+// magnitude are left undecided; the caller uses the filter only for sets
+// whose coordinates are all below 2^60, where the views are valid.
+__device__ __forceinline__ int orient_f32_filter(float2 A, float2 B, float2 C) {
+  const float M = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y))),
+                        fmaxf(fabsf(C.x), fabsf(C.y)));
+  if (!(M >= 8.6736174e-19f && M <= 1.1529215e+18f)) return 0;
+  const float u1 = __fsub_rn(B.x, A.x), v1 = __fsub_rn(B.y, A.y);
+  const float u2 = __fsub_rn(C.x, A.x), v2 = __fsub_rn(C.y, A.y);
+  const float U = fmaxf(fmaxf(fabsf(u1), fabsf(v1)), fmaxf(fabsf(u2), fabsf(v2)));
+  const float det = __fmaf_rn(u1, v2, -__fmul_rn(v1, u2));
+  const float mu = 5.9604645e-08f;                   // 2^-24
+  const float ed = __fadd_rn(__fmul_rn(2.3841870e-07f, M),        // 2 tau (1 + 3 tau) M, rounded up
+                             __fadd_rn(4.7020e-38f, __fmul_rn(6.0200692e-08f, U)));   // 4 eta + 1.01 mu U
+  const float e0 = __fadd_rn(__fadd_rn(__fmul_rn(4.f, __fmul_rn(ed, U)), __fmul_rn(2.f, __fmul_rn(ed, ed))),
+                             __fadd_rn(__fmul_rn(mu, __fmul_rn(U, U)), 5.6e-45f));
+  const float lhs = __fmul_rn(fabsf(det), 0.99999988f);          // (1 - 2 mu), rounded down
+  if (lhs > __fmul_rn(1.01f, e0)) return det > 0.f ? 1 : -1;
+  return 0;
+}
+
+// Exact orientation of float64 points, FP32-filtered first when `filt` (the
+// set's coordinates are below 2^60 and A, B, C are their f64_trunc_f32 views).
+__device__ __forceinline__ int orient_f64_views(double2 a, double2 b, double2 c, float2 A, float2 B,
+                                                float2 C, bool filt) {
+  if (filt) {
+    const int o = orient_f32_filter(A, B, C);
+    if (o) return o;
+  }
+  return orient_f64(a.x, a.y, b.x, b.y, c.x, c.y);
+}
+
+__device__ __forceinline__ float2 f64_view2(double2 p) {
+  return make_float2(f64_trunc_f32((uint64_t)__double_as_longlong(p.x)),
+                     f64_trunc_f32((uint64_t)__double_as_longlong(p.y)));
 }
 
 // ------------------------------------------------- memory-order helpers

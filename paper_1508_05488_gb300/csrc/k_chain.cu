@@ -30,32 +30,26 @@ template <>
 struct PT<DT_I32> { using T = int2; };
 
 template <int DT>
-__device__ __forceinline__ int orient_pts(const typename PT<DT>::T& a, const typename PT<DT>::T& b,
-                                          const typename PT<DT>::T& c, bool wide) {
-  if constexpr (DT == DT_F64) return orient_f64(a.x, a.y, b.x, b.y, c.x, c.y);
-  else return orient_i32(a.x, a.y, b.x, b.y, c.x, c.y, wide);
-}
-
-template <int DT>
 __device__ __forceinline__ bool same_pt(const typename PT<DT>::T& a, const typename PT<DT>::T& b) {
   return a.x == b.x && a.y == b.y;   // value equality: -0.0 == +0.0
 }
 
 // Merge two adjacent convex chains given by (head, tail) into the left one.
-// prv/nxt/alive/pt are accessed through the accessor `A` (shared or global).
-template <int DT, class A>
-__device__ void merge_chains(A& acc, int& hl, int& tl, int hr, int tr, bool wide) {
+// Links, flags, points and orientation go through the accessor (shared or
+// global memory).
+template <class A>
+__device__ void merge_chains(A& acc, int& hl, int& tl, int hr, int tr) {
   if (hr < 0) return;
   if (hl < 0) { hl = hr; tl = tr; return; }
   int a = tl, b = hr;
   for (;;) {
     bool moved = false;
-    while (a != hl && orient_pts<DT>(acc.pt(acc.prv(a)), acc.pt(a), acc.pt(b), wide) <= 0) {
+    while (a != hl && acc.orient(acc.prv(a), a, b) <= 0) {
       acc.kill(a);
       a = acc.prv(a);
       moved = true;
     }
-    while (b != tr && orient_pts<DT>(acc.pt(a), acc.pt(b), acc.pt(acc.nxt(b)), wide) <= 0) {
+    while (b != tr && acc.orient(a, b, acc.nxt(b)) <= 0) {
       acc.kill(b);
       b = acc.nxt(b);
       moved = true;
@@ -66,17 +60,33 @@ __device__ void merge_chains(A& acc, int& hl, int& tl, int hr, int tr, bool wide
   tl = tr;
 }
 
+// Orientation of three chain points: float64 through the FP32 filter on
+// their views (when the set's coordinates allow), then exactly; int32
+// exactly in 64/128-bit integers.
+template <int DT>
+__device__ __forceinline__ int orient_chain(const typename PT<DT>::T& a, const typename PT<DT>::T& b,
+                                            const typename PT<DT>::T& c, float2 A, float2 B, float2 C,
+                                            bool flag) {
+  if constexpr (DT == DT_F64) return orient_f64_views(a, b, c, A, B, C, flag);
+  else return orient_i32(a.x, a.y, b.x, b.y, c.x, c.y, flag);
+}
+
 template <int DT>
 struct SmemAcc {
   typename PT<DT>::T* p;
+  float2* f;          // FP32 views (float64 only)
   uint16_t* pv;
   uint16_t* nx;
   uint8_t* al;
-  __device__ __forceinline__ typename PT<DT>::T pt(int i) const { return p[i]; }
+  bool flag;          // float64: filter usable; int32: wide products
   __device__ __forceinline__ int prv(int i) const { return pv[i]; }
   __device__ __forceinline__ int nxt(int i) const { return nx[i]; }
   __device__ __forceinline__ void kill(int i) { al[i] = 0; }
   __device__ __forceinline__ void link(int a, int b) { nx[a] = (uint16_t)b; pv[b] = (uint16_t)a; }
+  __device__ __forceinline__ int orient(int i, int j, int k) const {
+    if constexpr (DT == DT_F64) return orient_chain<DT>(p[i], p[j], p[k], f[i], f[j], f[k], flag);
+    else return orient_chain<DT>(p[i], p[j], p[k], float2{}, float2{}, float2{}, flag);
+  }
 };
 
 template <int DT>
@@ -85,16 +95,22 @@ struct GlobAcc {
   uint32_t* pv;
   uint32_t* nx;
   uint8_t* al;
-  __device__ __forceinline__ typename PT<DT>::T pt(int i) const { return p[i]; }
+  bool flag;
   __device__ __forceinline__ int prv(int i) const { return (int)pv[i]; }
   __device__ __forceinline__ int nxt(int i) const { return (int)nx[i]; }
   __device__ __forceinline__ void kill(int i) { al[i] = 0; }
   __device__ __forceinline__ void link(int a, int b) { nx[a] = (uint32_t)b; pv[b] = (uint32_t)a; }
+  __device__ __forceinline__ int orient(int i, int j, int k) const {
+    const typename PT<DT>::T a = p[i], b = p[j], c = p[k];
+    if constexpr (DT == DT_F64) return orient_chain<DT>(a, b, c, f64_view2(a), f64_view2(b), f64_view2(c), flag);
+    else return orient_chain<DT>(a, b, c, float2{}, float2{}, float2{}, flag);
+  }
 };
 
 template <int DT>
 constexpr size_t chain_local_smem() {
-  return (size_t)kChainBlk * (sizeof(typename PT<DT>::T) + 2 + 2 + 2 + 1) + 2 * kThreads * sizeof(int);
+  return (size_t)kChainBlk * (sizeof(typename PT<DT>::T) + (DT == DT_F64 ? 8 : 0) + 2 + 2 + 2 + 1) +
+         2 * kThreads * sizeof(int);
 }
 
 template <int DT>
@@ -102,7 +118,8 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
   using P = typename PT<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   P* sp = reinterpret_cast<P*>(smem);
-  uint16_t* pv = reinterpret_cast<uint16_t*>(sp + kChainBlk);
+  float2* sf = reinterpret_cast<float2*>(sp + kChainBlk);              // views (float64 only)
+  uint16_t* pv = reinterpret_cast<uint16_t*>(DT == DT_F64 ? (void*)(sf + kChainBlk) : (void*)(sp + kChainBlk));
   uint16_t* nx = pv + kChainBlk;
   uint16_t* stk = nx + kChainBlk;
   int* gh = reinterpret_cast<int*>(stk + kChainBlk);
@@ -117,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
     const int s = g >> 2, r = g & 3;
     const SetDesc sd = get_set(j, s);
     const SetCtl& c = w.ctl[s];
-    const bool wide = (c.flags & SF_WIDE) != 0;
+    const bool flag = DT == DT_F64 ? (c.flags & SF_SMALL) != 0 : (c.flags & SF_WIDE) != 0;
     const uint32_t lb = b - w.chain_start[g];
     const uint32_t L = c.s2[r] + 2;
     const int64_t cb = chain_base(sd, s, c, r);
@@ -136,10 +153,12 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
         v = cp[cb + p];
       }
       sp[i] = v;
+      if constexpr (DT == DT_F64) sf[i] = f64_view2(v);
     }
     if (threadIdx.x == 0 && p0 > 0) pred = cp[cb + p0 - 1];
     __syncthreads();
 
+    SmemAcc<DT> acc{sp, sf, pv, nx, al, flag};
     // per thread: strict left-turn stack over its 16 positions
     const int i0 = threadIdx.x * kChainItems;
     const int i1 = min(m, i0 + kChainItems);
@@ -149,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
       if (i > 0) dup = same_pt<DT>(sp[i], sp[i - 1]);
       else dup = p0 > 0 && same_pt<DT>(sp[0], pred);
       if (dup) { al[i] = 0; continue; }
-      while (top >= 2 && orient_pts<DT>(sp[stk[i0 + top - 2]], sp[stk[i0 + top - 1]], sp[i], wide) <= 0) {
+      while (top >= 2 && acc.orient(stk[i0 + top - 2], stk[i0 + top - 1], i) <= 0) {
         al[stk[i0 + top - 1]] = 0;
         top--;
       }
@@ -163,13 +182,12 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
     gh[threadIdx.x] = top ? stk[i0] : -1;
     gt[threadIdx.x] = top ? stk[i0 + top - 1] : -1;
 
-    SmemAcc<DT> acc{sp, pv, nx, al};
     for (int step = 1; step < kThreads; step <<= 1) {
       __syncthreads();
       const int t = threadIdx.x;
       if ((t & (2 * step - 1)) == 0 && t + step < kThreads && (t + step) * kChainItems < m) {
         int hl = gh[t], tl = gt[t];
-        merge_chains<DT>(acc, hl, tl, gh[t + step], gt[t + step], wide);
+        merge_chains(acc, hl, tl, gh[t + step], gt[t + step]);
         gh[t] = hl;
         gt[t] = tl;
       }
@@ -201,15 +219,15 @@ __global__ void __launch_bounds__(kThreads) k_chain_merge(Job j, Ws w) {
     const int s = g >> 2, r = g & 3;
     const SetDesc sd = get_set(j, s);
     const SetCtl& c = w.ctl[s];
-    const bool wide = (c.flags & SF_WIDE) != 0;
+    const bool flag = DT == DT_F64 ? (c.flags & SF_SMALL) != 0 : (c.flags & SF_WIDE) != 0;
     const int64_t cb = chain_base(sd, s, c, r);
-    GlobAcc<DT> acc{reinterpret_cast<const P*>(w.cpts) + cb, w.cprev + cb, w.cnext + cb, w.calive + cb};
+    GlobAcc<DT> acc{reinterpret_cast<const P*>(w.cpts) + cb, w.cprev + cb, w.cnext + cb, w.calive + cb, flag};
     for (int step = 1; step < B; step <<= 1) {
       for (int q = threadIdx.x; (int64_t)q * 2 * step < B; q += kThreads) {
         int left = q * 2 * step, right = left + step;
         if (right >= B) continue;
         int hl = w.blk_head[b0 + left], tl = w.blk_tail[b0 + left];
-        merge_chains<DT>(acc, hl, tl, w.blk_head[b0 + right], w.blk_tail[b0 + right], wide);
+        merge_chains(acc, hl, tl, w.blk_head[b0 + right], w.blk_tail[b0 + right]);
         w.blk_head[b0 + left] = hl;
         w.blk_tail[b0 + left] = tl;
       }

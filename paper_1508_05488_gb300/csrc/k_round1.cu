@@ -106,12 +106,10 @@ __device__ __forceinline__ void cand_keys(uint32_t xh, uint32_t xl, uint32_t yh,
   }
 }
 
-// Fast-path compare: only the top 32 bits of k1 ... everything else in the
-// rare slow path (strict order: indices grow within a thread).
+// Key words of one point (int32: one word per coordinate, low words 0).
 template <int DT>
-__device__ __forceinline__ void a1_point(const typename PointT<DT>::T& p, uint32_t i, Lex best[4],
-                                         uint32_t th[4], uint32_t& amin) {
-  uint32_t xh, xl, yh, yl;
+__device__ __forceinline__ void a1_words(const typename PointT<DT>::T& p, uint32_t& xh, uint32_t& xl,
+                                         uint32_t& yh, uint32_t& yl, uint32_t& amin) {
   if constexpr (DT == DT_F64) {
     f64_key_words((uint64_t)__double_as_longlong(p.x), xh, xl, amin);
     f64_key_words((uint64_t)__double_as_longlong(p.y), yh, yl, amin);
@@ -120,19 +118,39 @@ __device__ __forceinline__ void a1_point(const typename PointT<DT>::T& p, uint32
     yh = (uint32_t)p.y ^ 0x80000000u;
     xl = yl = 0;
   }
-  if (xh <= th[0] || yh <= th[1] || ~xh <= th[2] || ~yh <= th[3]) {
+}
+
+// Whether a point can improve any of the four running minima: only the top
+// 32 bits of each k1 are compared here; the full comparison runs in
+// a1_update, which is rare (new minima, or ties of the top words).
+__device__ __forceinline__ bool a1_maybe(uint32_t xh, uint32_t yh, const uint32_t th[4]) {
+  return xh <= th[0] || yh <= th[1] || ~xh <= th[2] || ~yh <= th[3];
+}
+
+// Full update (indices grow within a thread: a strict order keeps the
+// smallest index among equal keys).
+template <int DT>
+__device__ __forceinline__ void a1_update(uint32_t xh, uint32_t xl, uint32_t yh, uint32_t yl, uint32_t i,
+                                          Lex best[4]) {
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-      Lex c;
-      cand_keys<DT>(xh, xl, yh, yl, e, c.k1, c.k2);
-      if (c.k1 < best[e].k1 || (c.k1 == best[e].k1 && c.k2 < best[e].k2)) {
-        best[e].k1 = c.k1;
-        best[e].k2 = c.k2;
-        best[e].idx = i;
-        th[e] = (uint32_t)(c.k1 >> 32);
-      }
+  for (int e = 0; e < 4; e++) {
+    Lex c;
+    cand_keys<DT>(xh, xl, yh, yl, e, c.k1, c.k2);
+    if (c.k1 < best[e].k1 || (c.k1 == best[e].k1 && c.k2 < best[e].k2)) {
+      best[e].k1 = c.k1;
+      best[e].k2 = c.k2;
+      best[e].idx = i;
     }
   }
+}
+
+// Thresholds shared by the warp: the smallest top word of each running
+// minimum over the lanes.  A point whose top word exceeds the warp's cannot
+// be the set's extreme, so only points at or below it take the full update;
+// sharing the bound across the warp keeps that rare.
+__device__ __forceinline__ void a1_thresholds(const Lex best[4], uint32_t th[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; e++) th[e] = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(best[e].k1 >> 32));
 }
 
 // Bucket of the stairs map: monotone non-decreasing in u.
@@ -229,6 +247,7 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
     double ym = fmax(fabs(c.ey[1]), fabs(c.ey[3]));
     const double lim = 1152921504606846976.0;  // 2^60
     small = xm <= lim && ym <= lim;
+    if (small) flags |= SF_SMALL;
     const bool filt = small && !(j.opts & OPT_NO_FILTER);
     if (filt) flags |= SF_FILTER;
     // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
@@ -304,18 +323,36 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; th[k] = 0xFFFFFFFFu; }
   uint32_t amin = 0x7FFFFFFFu;
 
+  // set-local indices fit in 32 bits (n <= 2^30)
   constexpr int U = 4;
-  for (int64_t base = c0; base < c1; base += (int64_t)kThreads * U) {
+  const uint32_t e0 = (uint32_t)c0, e1 = (uint32_t)c1;
+  for (uint32_t base = e0; base < e1; base += kThreads * U) {
     P v[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      int64_t i = base + u * kThreads + threadIdx.x;
-      if (i < c1) v[u] = __ldcs(pts + i);
+      const uint32_t i = base + u * kThreads + threadIdx.x;
+      if (i < e1) v[u] = __ldcs(pts + i);
     }
+    uint32_t xh[U], xl[U], yh[U], yl[U];
+    bool need = false;
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      int64_t i = base + u * kThreads + threadIdx.x;
-      if (i < c1) a1_point<DT>(v[u], (uint32_t)i, best, th, amin);
+      const uint32_t i = base + u * kThreads + threadIdx.x;
+      if (i < e1) {
+        a1_words<DT>(v[u], xh[u], xl[u], yh[u], yl[u], amin);
+        need |= a1_maybe(xh[u], yh[u], th);
+      } else {
+        xh[u] = yh[u] = 0xFFFFFFFFu;   // never read: need stays per point below
+      }
+    }
+    // rare: a warp-uniform branch keeps the full update out of the hot path
+    if (__any_sync(0xFFFFFFFFu, need)) {
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint32_t i = base + u * kThreads + threadIdx.x;
+        if (i < e1 && a1_maybe(xh[u], yh[u], th)) a1_update<DT>(xh[u], xl[u], yh[u], yl[u], i, best);
+      }
+      a1_thresholds(best, th);
     }
   }
 
@@ -580,6 +617,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
   __shared__ int st_tile[kClsStages], st_set[kClsStages], st_head[kClsStages];
   __shared__ uint32_t cnt[ITEMS][kWarps];
   __shared__ uint32_t bal[ITEMS][kWarps];
+  __shared__ uint16_t wq[kWarps][ITEMS * 32];     // pass-3 queue: region-1 << 9 | item << 5 | lane
+  __shared__ uint32_t wdrop[kWarps][ITEMS];
   __shared__ uint32_t rcnt[4];
   __shared__ int sh_set, sh_status;
   __shared__ uint32_t sh_flags;
@@ -685,45 +724,94 @@ __global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
     const bool skip_set = sh_status != 0;
     const uint32_t* pre = w.stairs + (size_t)s * 4 * kStairB;
 
-    uint64_t regs = 0;    // 4 bits per item
+    // pass 1, every point, branch-free: region code per item (4 bits):
+    // 0 inside or on the quadrilateral, 1..4 the region, 15 undecided
+    const int npv = skip_set ? 0 : np;
+    uint64_t regs = 0;
+    uint32_t und = 0, outm = 0;    // item bitmasks
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
       const int i = k * kThreads + tid;
-      int r = 0;
-      if (i < np && !skip_set) {
-        const P p = *reinterpret_cast<const P*>(base + (size_t)i * PB);
-        float X, Y;
-        f32_view<DT>(p, X, Y);
+      uint32_t r = 0;
+      if (i < npv) {
+        const P p = *reinterpret_cast<const P*>(base + i * PB);
         if constexpr (DT == DT_F64) {
-          float d0 = __fmaf_rn(fA[0], Y, __fmaf_rn(fB[0], X, fC[0]));
-          float d1 = __fmaf_rn(fA[1], Y, __fmaf_rn(fB[1], X, fC[1]));
-          float d2 = __fmaf_rn(fA[2], Y, __fmaf_rn(fB[2], X, fC[2]));
-          float d3 = __fmaf_rn(fA[3], Y, __fmaf_rn(fB[3], X, fC[3]));
-          r = d0 < -fE[0] ? 1 : !(d0 > fE[0]) ? -1
-            : d1 < -fE[1] ? 2 : !(d1 > fE[1]) ? -1
-            : d2 < -fE[2] ? 3 : !(d2 > fE[2]) ? -1
-            : d3 < -fE[3] ? 4 : !(d3 > fE[3]) ? -1 : 0;
-          if (r < 0) r = region_exact_f64(p.x, p.y, sh_ex, sh_ey, flags);
+          float X, Y;
+          f32_view<DT>(p, X, Y);
+          const float d0 = __fmaf_rn(fA[0], Y, __fmaf_rn(fB[0], X, fC[0]));
+          const float d1 = __fmaf_rn(fA[1], Y, __fmaf_rn(fB[1], X, fC[1]));
+          const float d2 = __fmaf_rn(fA[2], Y, __fmaf_rn(fB[2], X, fC[2]));
+          const float d3 = __fmaf_rn(fA[3], Y, __fmaf_rn(fB[3], X, fC[3]));
+          // first edge not certainly inside decides: outside -> region,
+          // undecided -> 15
+          r = !(d3 > fE[3]) ? (d3 < -fE[3] ? 4u : 15u) : 0u;
+          r = !(d2 > fE[2]) ? (d2 < -fE[2] ? 3u : 15u) : r;
+          r = !(d1 > fE[1]) ? (d1 < -fE[1] ? 2u : 15u) : r;
+          r = !(d0 > fE[0]) ? (d0 < -fE[0] ? 1u : 15u) : r;
         } else {
           if (flags & SF_WIDE) {
-            r = region_exact_i32_wide(p.x, p.y, sh_ix, sh_iy, flags);
+            r = 15u;
           } else {
 #pragma unroll
             for (int q = 3; q >= 0; q--) {
               if (!(flags & (SF_DEGEN0 << q)) &&
                   orient_i32(ix[q], iy[q], ix[(q + 1) & 3], iy[(q + 1) & 3], p.x, p.y, false) < 0)
-                r = q + 1;
+                r = (uint32_t)q + 1;
             }
           }
         }
-        if (r > 0 && stairs_on) {
-          const int q = r - 1;
-          const int b = stair_bucket(sort_u(X, Y, q), slo[q], ssc[q]);
-          if (cmp_key_hi<DT>(p, q) > __ldg(pre + q * kStairB + b)) r = 0;   // dominated
-        }
       }
       regs |= (uint64_t)r << (4 * k);
-      const uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
+      und |= (uint32_t)(r == 15u) << k;
+      outm |= (uint32_t)(r - 1u < 4u) << k;
+    }
+    // pass 2, rare: exact region test of the points the filter left open
+    if (__any_sync(0xFFFFFFFFu, und != 0)) {
+#pragma unroll
+      for (int k = 0; k < ITEMS; k++) {
+        if ((und >> k) & 1u) {
+          const P p = *reinterpret_cast<const P*>(base + (k * kThreads + tid) * PB);
+          uint32_t r;
+          if constexpr (DT == DT_F64) r = (uint32_t)region_exact_f64(p.x, p.y, sh_ex, sh_ey, flags);
+          else r = (uint32_t)region_exact_i32_wide(p.x, p.y, sh_ix, sh_iy, flags);
+          regs = (regs & ~(0xFull << (4 * k))) | ((uint64_t)r << (4 * k));
+          outm |= (uint32_t)(r != 0) << k;
+        }
+      }
+    }
+    // pass 3: dominance prefilter of the region points.  The warp queues its
+    // (item, lane) pairs with a region and works through the queue densely,
+    // so the cost follows the number of region points, not the items.
+    if (stairs_on && __any_sync(0xFFFFFFFFu, outm != 0)) {
+      uint16_t* q = wq[warp];
+      uint32_t nq = 0;
+      const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+      for (int k = 0; k < ITEMS; k++) {
+        const bool o = (outm >> k) & 1u;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, o);
+        if (o) q[nq + __popc(b & lt_mask)] = (uint16_t)(((((regs >> (4 * k)) & 0xFull) - 1ull) << 9) | (k << 5) | lane);
+        nq += __popc(b);
+      }
+      if (lane < ITEMS) wdrop[warp][lane] = 0;
+      __syncwarp();
+      for (uint32_t e = lane; e < nq; e += 32) {
+        const uint32_t en = q[e];
+        const int qr = (int)(en >> 9) & 3, k = (int)(en >> 5) & 15, l = (int)(en & 31);
+        const P p = *reinterpret_cast<const P*>(base + (k * kThreads + warp * 32 + l) * PB);
+        float X, Y;
+        f32_view<DT>(p, X, Y);
+        const int b = stair_bucket(sort_u(X, Y, qr), slo[qr], ssc[qr]);
+        if (cmp_key_hi<DT>(p, qr) > __ldg(pre + qr * kStairB + b)) atomicOr(&wdrop[warp][k], 1u << l);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < ITEMS; k++)
+        if ((wdrop[warp][k] >> lane) & 1u) regs &= ~(0xFull << (4 * k));      // dominated
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, ((regs >> (4 * k)) & 0xFull) != 0);
       if (lane == 0) { cnt[k][warp] = __popc(b); bal[k][warp] = b; }
     }
     __syncthreads();
@@ -758,6 +846,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
     if (regs) {
       uint64_t* keys = w.keyB + sd.off + t0;
       uint32_t* vals = w.valB + sd.off + t0;
+      uint64_t* spv = w.spvB + sd.off + t0;
       const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
       for (int k = 0; k < ITEMS; k++) {
@@ -769,6 +858,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
           const uint32_t pos = cnt[k][warp] + __popc(b & lt_mask);
           keys[pos] = sort_key<DT>(p, r);
           vals[pos] = ((uint32_t)(r - 1) << 30) | (uint32_t)(t0 + i);
+          if constexpr (DT == DT_F64) spv[pos] = spa_v_f64(p.x, p.y, r - 1);
+          else spv[pos] = spa_v_i32(p.x, p.y, r - 1);
           atomicAdd(&rcnt[r - 1], 1u);
         }
       }
@@ -777,6 +868,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
     if (tid == 0) {
       w.tcnt[tile] = (uint64_t)rcnt[0] | ((uint64_t)rcnt[1] << 16) | ((uint64_t)rcnt[2] << 32) |
                      ((uint64_t)rcnt[3] << 48);
+      uint32_t* pt = reinterpret_cast<uint32_t*>(w.ptot + sd.chunkP + (int)(lt / kPlanTiles));
+      for (int q = 0; q < 4; q++)
+        if (rcnt[q]) atomicAdd(pt + q, rcnt[q]);
       fence_async_smem();
       issue(slot);
     }
@@ -797,54 +891,75 @@ __global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
   __shared__ uint32_t carry[4];
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int s = blockIdx.x; s < j.nsets; s += gridDim.x) {
-    const SetDesc sd = get_set(j, s);
-    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < sd.ntile2; b0 += kThreads) {
-      const int t = b0 + threadIdx.x;
-      uint64_t c = t < sd.ntile2 ? w.tcnt[sd.tile2 + t] : 0ull;
-      uint32_t v[4], x[4];
-#pragma unroll
-      for (int r = 0; r < 4; r++) { v[r] = (uint32_t)(c >> (16 * r)) & 0xFFFFu; x[r] = v[r]; }
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-          uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[r], o);
-          if (lane >= o) x[r] += y;
-        }
-      }
-      if (lane == 31)
-        for (int r = 0; r < 4; r++) wsum[r][warp] = x[r];
-      __syncthreads();
-      uint32_t pre[4];
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        pre[r] = carry[r];
-        for (int q = 0; q < warp; q++) pre[r] += wsum[r][q];
-      }
-      if (t < sd.ntile2)
-        w.toff[sd.tile2 + t] = make_uint4(pre[0] + x[0] - v[0], pre[1] + x[1] - v[1],
-                                          pre[2] + x[2] - v[2], pre[3] + x[3] - v[3]);
-      __syncthreads();
-      if (threadIdx.x == kThreads - 1)
-        for (int r = 0; r < 4; r++) carry[r] = pre[r] + x[r];
-      __syncthreads();
+  const int chunk = blockIdx.x;
+  int s = 0;
+  if (j.sets) {
+    int lo = 0, hi = j.nsets - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (j.sets[mid].chunkP <= chunk) lo = mid; else hi = mid - 1;
     }
-    if (threadIdx.x == 0) {
-      SetCtl& c = w.ctl[s];
-      uint32_t s1 = 0;
-      bool big = false;
-      for (int r = 0; r < 4; r++) {
-        c.cnt[r] = carry[r];
-        s1 += carry[r];
-        big |= carry[r] > (uint32_t)kSmallMax;
-      }
-      c.s1 = s1;
-      if (big) c.flags |= SF_BIG;
+    s = lo;
+  }
+  const SetDesc sd = get_set(j, s);
+  const int lc = chunk - sd.chunkP;
+  // per-region survivors of the set's earlier chunks (a2 added them up)
+  if (threadIdx.x < 4) {
+    uint32_t b = 0;
+    const uint32_t* pt = reinterpret_cast<const uint32_t*>(w.ptot + sd.chunkP);
+    for (int q = 0; q < lc; q++) b += pt[4 * q + threadIdx.x];
+    carry[threadIdx.x] = b;
+  }
+  __syncthreads();
+  constexpr int per = kPlanTiles / kThreads;
+  const int t0 = lc * kPlanTiles + threadIdx.x * per;     // set-local tiles of this thread
+  uint32_t v[per][4], own[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < per; q++) {
+    const int t = t0 + q;
+    const uint64_t c = t < sd.ntile2 ? w.tcnt[sd.tile2 + t] : 0ull;
+#pragma unroll
+    for (int r = 0; r < 4; r++) { v[q][r] = (uint32_t)(c >> (16 * r)) & 0xFFFFu; own[r] += v[q][r]; }
+  }
+  uint32_t x[4];
+#pragma unroll
+  for (int r = 0; r < 4; r++) x[r] = own[r];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[r], o);
+      if (lane >= o) x[r] += y;
     }
-    __syncthreads();
+  }
+  if (lane == 31)
+    for (int r = 0; r < 4; r++) wsum[r][warp] = x[r];
+  __syncthreads();
+  uint32_t run[4];
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    run[r] = carry[r] + x[r] - own[r];
+    for (int q = 0; q < warp; q++) run[r] += wsum[r][q];
+  }
+#pragma unroll
+  for (int q = 0; q < per; q++) {
+    const int t = t0 + q;
+    if (t < sd.ntile2) w.toff[sd.tile2 + t] = make_uint4(run[0], run[1], run[2], run[3]);
+#pragma unroll
+    for (int r = 0; r < 4; r++) run[r] += v[q][r];
+  }
+  if (lc == sd.nchunkP - 1 && threadIdx.x == kThreads - 1) {
+    // the set's last chunk: run[] now holds the set's totals
+    SetCtl& c = w.ctl[s];
+    uint32_t s1 = 0;
+    bool big = false;
+    for (int r = 0; r < 4; r++) {
+      c.cnt[r] = run[r];
+      s1 += run[r];
+      big |= run[r] > (uint32_t)kSmallMax;
+    }
+    c.s1 = s1;
+    if (big) c.flags |= SF_BIG;
   }
   // last CTA: plan the multi-CTA sort (big sets) and list the small segments
   __syncthreads();
@@ -902,6 +1017,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
       const bool ok = i < n;
       const uint64_t key = ok ? w.keyB[src + i] : 0;
       const uint32_t val = ok ? w.valB[src + i] : 0;
+      const uint64_t spv = ok ? w.spvB[src + i] : 0;
       const int r = ok ? (int)(val >> 30) : -1;
 #pragma unroll
       for (int q = 0; q < 4; q++) {
@@ -910,6 +1026,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
           const uint32_t pos = base[q] + __popc(b & lt_mask);
           w.keyA[sd.off + pos] = key;
           w.valA[sd.off + pos] = val;
+          w.spvA[sd.off + pos] = spv;
         }
         base[q] += __popc(b);
       }
@@ -939,8 +1056,7 @@ int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
 }
 
 int launch_gather(const Job& j, const Ws& w, const Launch& L) {
-  int gp = j.nsets < L.grid_cap ? j.nsets : L.grid_cap;
-  k_plan<<<gp < 1 ? 1 : gp, kThreads, 0, L.stream>>>(j, w);
+  k_plan<<<j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream>>>(j, w);
   int gg = (j.ntile2 + kWarps - 1) / kWarps;
   if (gg > L.grid_cap) gg = L.grid_cap;
   if (gg < 1) gg = 1;

@@ -33,7 +33,7 @@ namespace cch {
 namespace {
 
 constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 17;   // 131072 points
-constexpr size_t kNoAllocBytes = size_t(8) << 20;         // 8 MiB
+constexpr size_t kNoAllocBytes = size_t(12) << 20;        // 12 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -61,6 +61,7 @@ size_t na_layout(int64_t n, int32_t nchunk1, int32_t ntile2, char* base, Ws& w, 
   w = Ws{};
   w.ctl = (SetCtl*)take(sizeof(SetCtl));
   w.ctr = (uint32_t*)take(sizeof(uint32_t) * CT_COUNT);
+  w.ptot = (uint4*)take(16 * ((size_t)ntile2 / kPlanTiles + 2));
   ctl_bytes = o;
   status_off = o;
   w.st_sort = (uint64_t*)take(8 * 256 * (size_t)sort_tiles);
@@ -76,6 +77,8 @@ size_t na_layout(int64_t n, int32_t nchunk1, int32_t ntile2, char* base, Ws& w, 
   w.keyB = (uint64_t*)take(8 * (size_t)n);
   w.valA = (uint32_t*)take(4 * (size_t)n);
   w.valB = (uint32_t*)take(4 * (size_t)n);
+  w.spvA = (uint64_t*)take(8 * (size_t)n);
+  w.spvB = (uint64_t*)take(8 * (size_t)n);
   w.hist = (uint32_t*)take(4 * (size_t)kSortPasses * 256);
   w.sort_start = (uint32_t*)take(8);
   w.spa_start = (uint32_t*)take(4 * 5);
@@ -132,8 +135,9 @@ extern "C" int cch_hull_noalloc(const void* points, int64_t n, int dtype, int32_
   j.nchunk1 = (int32_t)((n + len - 1) / len);
   j.ntile2 = (int32_t)((n + cls_tile(dtype) - 1) / cls_tile(dtype));
   j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
+  j.nchunkP = (j.ntile2 + kPlanTiles - 1) / kPlanTiles;
   j.sets = nullptr;
-  j.one = SetDesc{0, n, 0, j.nchunk1, 0, j.ntile2, 0, j.nchunk3};
+  j.one = SetDesc{0, n, 0, j.nchunk1, 0, j.ntile2, 0, j.nchunk3, 0, j.nchunkP};
 
   // set-up, once per device with that device current: the array's address
   if (!g_na_ptr[dev]) {
