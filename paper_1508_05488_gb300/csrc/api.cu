@@ -63,8 +63,8 @@ Layout layout(const Dims& d, char* base) {
   L.w.st_out = (uint64_t*)take(8 * (size_t)d.max_out_tiles);
   L.status_bytes = o - L.status_off;
   L.w.part = (Part*)take(sizeof(Part) * (size_t)std::max(d.nchunk1, 1));
-  L.w.tcnt = (uint64_t*)take(8 * (size_t)std::max(d.ntile2, 1));
-  L.w.toff = (uint4*)take(16 * (size_t)std::max(d.ntile2, 1));
+  L.w.tcnt = (uint64_t*)take(8 * 8 * (size_t)std::max(d.ntile2, 1));
+  L.w.toff = (uint4*)take(16 * 8 * (size_t)std::max(d.ntile2, 1));
   L.w.small_seg = (uint32_t*)take(4 * 4 * (size_t)d.nsets);
   L.w.keyA = (uint64_t*)take(8 * (size_t)d.N);
   L.w.keyB = (uint64_t*)take(8 * (size_t)d.N);

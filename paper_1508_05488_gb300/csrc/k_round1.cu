@@ -568,14 +568,20 @@ __device__ __noinline__ int region_exact_f64(double px, double py, const double*
   return 0;
 }
 
-__device__ __noinline__ int region_exact_i32_wide(int px, int py, const int* ix, const int* iy,
+__device__ __noinline__ int region_exact_i32_wide(int px, int py, const double* ex, const double* ey,
                                                   uint32_t flags) {
   for (int k = 0; k < 4; k++) {
     if (flags & (SF_DEGEN0 << k)) continue;
     int k1 = (k + 1) & 3;
-    if (orient_i32(ix[k], iy[k], ix[k1], iy[k1], px, py, true) < 0) return k + 1;
+    if (orient_i32((int)ex[k], (int)ey[k], (int)ex[k1], (int)ey[k1], px, py, true) < 0) return k + 1;
   }
   return 0;
+}
+
+// Element r (0..3) of a four-element register array without dynamic
+// indexing (which would move the array to local memory).
+__device__ __forceinline__ float sel4(const float (&a)[4], int r) {
+  return r == 0 ? a[0] : r == 1 ? a[1] : r == 2 ? a[2] : a[3];
 }
 
 // Table 1 sort key of a region-r point (r = 1..4): R1 x asc, R2 y asc,
@@ -600,288 +606,285 @@ __device__ __forceinline__ uint64_t sort_key(const typename PointT<DT>::T& p, in
   }
 }
 
+constexpr int kClsConsumers = 8;                   // consumer warps of a2
+constexpr int kClsBlock = (kClsConsumers + 1) * 32;  // + one producer warp
+
 template <int DT>
 constexpr int cls_smem_bytes() {
   return kClsStages * (kClsTileBytes + 16);
 }
 
+// Set parameters a consumer warp keeps in registers (the per-point filter);
+// the rest lives in the warp's shared-memory copy (WarpParams).
+struct ClsParams {
+  float fA[4], fB[4], fC[4], fE[4];
+  uint32_t flags;
+  int32_t status;
+};
+struct WarpParams {
+  float slo[4], ssc[4];
+  int ix[4], iy[4];
+};
+
+// a2.  Warp-specialised: warp 8 acquires tiles (in increasing order) and
+// streams them into a ring of shared-memory stages with 1-D TMA bulk copies
+// (full/empty mbarriers); warps 0..7 each classify a contiguous eighth of the
+// tile, so (warp, item, lane) is point order, and compact their survivors
+// into their own sub-slot of the tile's record range (index order within the
+// sub-slot) -- no block-wide barrier on the per-tile path.
 template <int DT>
-__global__ void __launch_bounds__(kThreads, 2) k_classify(Job j, Ws w) {
+__global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
   using P = typename PointT<DT>::T;
   constexpr int PB = (int)sizeof(P);
   constexpr int TILE = kClsTileBytes / PB;
-  constexpr int ITEMS = TILE / kThreads;
-  constexpr int SB = kClsTileBytes + 16;        // stage bytes (16 bytes of slack in front)
+  constexpr int WPTS = TILE / kClsConsumers;          // points per consumer warp
+  constexpr int IW = WPTS / 32;                       // items per lane
+  constexpr int SB = kClsTileBytes + 16;              // stage bytes (16 bytes of slack in front)
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[kClsStages];
+  __shared__ __align__(8) uint64_t full[kClsStages], empty[kClsStages];
   __shared__ int st_tile[kClsStages], st_set[kClsStages], st_head[kClsStages];
-  __shared__ uint32_t cnt[ITEMS][kWarps];
-  __shared__ uint32_t bal[ITEMS][kWarps];
-  __shared__ uint16_t wq[kWarps][ITEMS * 32];     // pass-3 queue: region-1 << 9 | item << 5 | lane
-  __shared__ uint32_t wdrop[kWarps][ITEMS];
-  __shared__ uint32_t rcnt[4];
-  __shared__ int sh_set, sh_status;
-  __shared__ uint32_t sh_flags;
-  __shared__ float sh_f[4][4];
-  __shared__ float sh_st[3][4];
-  __shared__ double sh_ex[4], sh_ey[4];
-  __shared__ int sh_ix[4], sh_iy[4];
+  __shared__ uint16_t wq[kClsConsumers][IW * 32];     // pass-2 queue: int32 region << 9 | item << 5 | lane
+  __shared__ uint8_t wrk[kClsConsumers][IW * 32];     // pass-2 result: region of (item, lane)
+  __shared__ WarpParams wpar[kClsConsumers];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  // producer: acquire the next tile and start its copy into `slot`
-  auto issue = [&](int slot) {
-    const uint32_t t = atomicAdd(w.ctr + CT_CLS_TILE, 1u);
-    st_tile[slot] = (int)t;
-    if (t >= (uint32_t)j.ntile2) return;
-    int s = 0;
-    if (j.sets) {
-      int lo = 0, hi = j.nsets - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (j.sets[mid].tile2 <= (int)t) lo = mid; else hi = mid - 1;
-      }
-      s = lo;
-    }
-    st_set[slot] = s;
-    const SetDesc sd = get_set(j, s);
-    const int64_t i0 = (int64_t)(t - sd.tile2) * TILE;
-    const int np = (int)min((int64_t)TILE, sd.n - i0);
-    const char* src = reinterpret_cast<const char*>(j.pts) + (sd.off + i0) * PB;
-    unsigned char* dst = smem + slot * SB + 16;
-    const int head = ((uintptr_t)src & 15) ? 1 : 0;       // int32 only
-    const int rem = np - head;
-    const int tail = ((rem * PB) & 15) ? 1 : 0;
-    const uint32_t bytes = (uint32_t)(rem - tail) * PB;
-    st_head[slot] = head;
-    if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
-    if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
-    mbar_arrive_tx(&bar[slot], bytes);
-    if (bytes) tma_load_1d(dst, src + head * PB, bytes, &bar[slot]);
-  };
-
   if (tid == 0) {
-    for (int q = 0; q < kClsStages; q++) mbar_init(&bar[q], 1);
+    for (int q = 0; q < kClsStages; q++) { mbar_init(&full[q], 1); mbar_init(&empty[q], kClsConsumers); }
     fence_mbar_init();
     fence_async_smem();
-    sh_set = -1;
   }
   __syncthreads();
-  if (tid == 0)
-    for (int q = 0; q < kClsStages; q++) issue(q);
-  __syncthreads();
 
-  float fA[4], fB[4], fC[4], fE[4], slo[4], ssc[4];
-  int ix[4], iy[4];
-  uint32_t flags = 0;
-  bool stairs_on = false;
+  if (warp == kClsConsumers) {
+    // ---------------------------------------------------------- producer
+    if (lane != 0) return;
+    int issued = 0;
+    bool ok = true;
+    for (int it = 0;; it++) {
+      const int slot = it % kClsStages;
+      if (it >= kClsStages) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&empty[slot], (uint32_t)((it / kClsStages) - 1) & 1u))
+          if (!spin_step(spins, w.ctr)) { ok = false; break; }
+        if (!ok) break;
+        fence_async_smem();
+      }
+      const uint32_t t = atomicAdd(w.ctr + CT_CLS_TILE, 1u);
+      st_tile[slot] = (int)t;
+      if (t >= (uint32_t)j.ntile2) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&full[slot])) : "memory");
+        break;
+      }
+      int s = 0;
+      if (j.sets) {
+        int lo = 0, hi = j.nsets - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (j.sets[mid].tile2 <= (int)t) lo = mid; else hi = mid - 1;
+        }
+        s = lo;
+      }
+      st_set[slot] = s;
+      const SetDesc sd = get_set(j, s);
+      const int64_t i0 = (int64_t)(t - sd.tile2) * TILE;
+      const int np = (int)min((int64_t)TILE, sd.n - i0);
+      const char* src = reinterpret_cast<const char*>(j.pts) + (sd.off + i0) * PB;
+      unsigned char* dst = smem + slot * SB + 16;
+      const int head = ((uintptr_t)src & 15) ? 1 : 0;       // int32 only
+      const int rem = np - head;
+      const int tail = ((rem * PB) & 15) ? 1 : 0;
+      const uint32_t bytes = (uint32_t)(rem - tail) * PB;
+      st_head[slot] = head;
+      if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
+      if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
+      mbar_arrive_tx(&full[slot], bytes);
+      if (bytes) tma_load_1d(dst, src + head * PB, bytes, &full[slot]);
+      issued = it + 1;
+    }
+    if (!ok) {
+      // a wait ran out: let the copies already issued land before exiting
+      for (int it = max(0, issued - kClsStages); it < issued; it++) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&full[it % kClsStages], (uint32_t)(it / kClsStages) & 1u))
+          if (!spin_step(spins, w.ctr) && spins > kSpinLimit) break;
+      }
+    }
+    return;
+  }
 
+  // ------------------------------------------------------------ consumers
+  ClsParams cp{};
+  int cur_set = -1;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   for (int it = 0;; it++) {
     const int slot = it % kClsStages;
-    const uint32_t parity = (uint32_t)(it / kClsStages) & 1u;
+    {
+      uint32_t spins = 0;
+      bool ok = true;
+      while (!mbar_try_wait(&full[slot], (uint32_t)(it / kClsStages) & 1u))
+        if (!spin_step(spins, w.ctr)) { ok = false; break; }
+      if (!ok) break;
+    }
     const int tile = st_tile[slot];
     if (tile >= j.ntile2) break;
     const int s = st_set[slot];
     const SetDesc sd = get_set(j, s);
-    if (s != sh_set) {            // uniform: a new set's parameters
-      __syncthreads();
-      if (tid == 0) {
-        const SetCtl& c = w.ctl[s];
-        for (int k = 0; k < 4; k++) {
-          sh_f[0][k] = c.fA[k]; sh_f[1][k] = -c.fB[k]; sh_f[2][k] = c.fC[k]; sh_f[3][k] = c.fE[k];
-          sh_st[0][k] = c.slo[k]; sh_st[1][k] = c.sscale[k];
-          sh_ex[k] = c.ex[k]; sh_ey[k] = c.ey[k];
-          sh_ix[k] = (int)c.ex[k]; sh_iy[k] = (int)c.ey[k];
-        }
-        sh_flags = c.flags;
-        sh_status = c.status;
-        sh_set = s;
-      }
-      __syncthreads();
+    WarpParams& wp = wpar[warp];
+    if (s != cur_set) {
+      const SetCtl& c = w.ctl[s];
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        fA[k] = sh_f[0][k]; fB[k] = sh_f[1][k]; fC[k] = sh_f[2][k]; fE[k] = sh_f[3][k];
-        slo[k] = sh_st[0][k]; ssc[k] = sh_st[1][k];
-        ix[k] = sh_ix[k]; iy[k] = sh_iy[k];
+        cp.fA[k] = c.fA[k]; cp.fB[k] = -c.fB[k]; cp.fC[k] = c.fC[k]; cp.fE[k] = c.fE[k];
       }
-      flags = sh_flags;
-      stairs_on = (flags & SF_STAIRS) != 0;
-    }
-    // wait for the tile (bounded; a copy always completes unless the device
-    // is failing, in which case the call reports CCH_ERR_TIMEOUT)
-    {
-      uint32_t spins = 0;
-      bool ok = true;
-      while (!mbar_try_wait(&bar[slot], parity)) {
-        if (!spin_step(spins, w.ctr)) { ok = false; break; }
+      if (lane < 4) {
+        wp.slo[lane] = c.slo[lane]; wp.ssc[lane] = c.sscale[lane];
+        wp.ix[lane] = (int)c.ex[lane]; wp.iy[lane] = (int)c.ey[lane];
       }
-      if (!ok) { __syncthreads(); break; }
+      __syncwarp();
+      cp.flags = c.flags;
+      cp.status = c.status;
+      cur_set = s;
     }
     const int64_t lt = tile - sd.tile2;
     const int64_t t0 = lt * TILE;
     const int np = (int)min((int64_t)TILE, sd.n - t0);
     const unsigned char* base = smem + slot * SB + 16 - st_head[slot] * PB;
-    const bool skip_set = sh_status != 0;
+    const int wb = warp * WPTS;                    // this warp's first point in the tile
+    const int npv = cp.status != 0 ? 0 : np;
     const uint32_t* pre = w.stairs + (size_t)s * 4 * kStairB;
+    const SetCtl& cg = w.ctl[s];
 
-    // pass 1, every point, branch-free: region code per item (4 bits):
-    // 0 inside or on the quadrilateral, 1..4 the region, 15 undecided
-    const int npv = skip_set ? 0 : np;
-    uint64_t regs = 0;
-    uint32_t und = 0, outm = 0;    // item bitmasks
-#pragma unroll
-    for (int k = 0; k < ITEMS; k++) {
-      const int i = k * kThreads + tid;
-      uint32_t r = 0;
+    // pass 1, every point: is it certainly inside the quadrilateral?
+    // (float64: the FP32 filter's four edge tests; int32: the exact region)
+    uint32_t nim = 0;                              // items that need pass 2
+    uint32_t ireg[IW > 8 ? 2 : 1] = {};            // int32: exact region, 4 bits per item
+#pragma unroll 4
+    for (int k = 0; k < IW; k++) {
+      const int i = wb + k * 32 + lane;
       if (i < npv) {
         const P p = *reinterpret_cast<const P*>(base + i * PB);
         if constexpr (DT == DT_F64) {
           float X, Y;
           f32_view<DT>(p, X, Y);
-          const float d0 = __fmaf_rn(fA[0], Y, __fmaf_rn(fB[0], X, fC[0]));
-          const float d1 = __fmaf_rn(fA[1], Y, __fmaf_rn(fB[1], X, fC[1]));
-          const float d2 = __fmaf_rn(fA[2], Y, __fmaf_rn(fB[2], X, fC[2]));
-          const float d3 = __fmaf_rn(fA[3], Y, __fmaf_rn(fB[3], X, fC[3]));
-          // first edge not certainly inside decides: outside -> region,
-          // undecided -> 15
-          r = !(d3 > fE[3]) ? (d3 < -fE[3] ? 4u : 15u) : 0u;
-          r = !(d2 > fE[2]) ? (d2 < -fE[2] ? 3u : 15u) : r;
-          r = !(d1 > fE[1]) ? (d1 < -fE[1] ? 2u : 15u) : r;
-          r = !(d0 > fE[0]) ? (d0 < -fE[0] ? 1u : 15u) : r;
+          const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
+          const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
+          const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
+          const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
+          const bool in = (d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3]);
+          nim |= (uint32_t)(!in) << k;
         } else {
-          if (flags & SF_WIDE) {
+          uint32_t r = 0;
+          if (cp.flags & SF_WIDE) {
             r = 15u;
           } else {
 #pragma unroll
             for (int q = 3; q >= 0; q--) {
-              if (!(flags & (SF_DEGEN0 << q)) &&
-                  orient_i32(ix[q], iy[q], ix[(q + 1) & 3], iy[(q + 1) & 3], p.x, p.y, false) < 0)
+              if (!(cp.flags & (SF_DEGEN0 << q)) &&
+                  orient_i32(wp.ix[q], wp.iy[q], wp.ix[(q + 1) & 3], wp.iy[(q + 1) & 3], p.x, p.y, false) < 0)
                 r = (uint32_t)q + 1;
             }
           }
-        }
-      }
-      regs |= (uint64_t)r << (4 * k);
-      und |= (uint32_t)(r == 15u) << k;
-      outm |= (uint32_t)(r - 1u < 4u) << k;
-    }
-    // pass 2, rare: exact region test of the points the filter left open
-    if (__any_sync(0xFFFFFFFFu, und != 0)) {
-#pragma unroll
-      for (int k = 0; k < ITEMS; k++) {
-        if ((und >> k) & 1u) {
-          const P p = *reinterpret_cast<const P*>(base + (k * kThreads + tid) * PB);
-          uint32_t r;
-          if constexpr (DT == DT_F64) r = (uint32_t)region_exact_f64(p.x, p.y, sh_ex, sh_ey, flags);
-          else r = (uint32_t)region_exact_i32_wide(p.x, p.y, sh_ix, sh_iy, flags);
-          regs = (regs & ~(0xFull << (4 * k))) | ((uint64_t)r << (4 * k));
-          outm |= (uint32_t)(r != 0) << k;
+          ireg[k >> 3] |= r << (4 * (k & 7));
+          nim |= (uint32_t)(r != 0) << k;
         }
       }
     }
-    // pass 3: dominance prefilter of the region points.  The warp queues its
-    // (item, lane) pairs with a region and works through the queue densely,
-    // so the cost follows the number of region points, not the items.
-    if (stairs_on && __any_sync(0xFFFFFFFFu, outm != 0)) {
+    // pass 2, dense over the warp's remaining points (a queue): region,
+    // exact test where the filter was undecided, dominance prefilter
+    uint64_t regs = 0;
+    if (__any_sync(0xFFFFFFFFu, nim != 0)) {
       uint16_t* q = wq[warp];
+      uint8_t* rk = wrk[warp];
       uint32_t nq = 0;
-      const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-      for (int k = 0; k < ITEMS; k++) {
-        const bool o = (outm >> k) & 1u;
+      for (int k = 0; k < IW; k++) {
+        const bool o = (nim >> k) & 1u;
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, o);
-        if (o) q[nq + __popc(b & lt_mask)] = (uint16_t)(((((regs >> (4 * k)) & 0xFull) - 1ull) << 9) | (k << 5) | lane);
+        if (o) {
+          uint32_t en = (uint32_t)(k << 5) | lane;
+          if constexpr (DT == DT_I32) en |= ((ireg[k >> 3] >> (4 * (k & 7))) & 0xFu) << 9;
+          q[nq + __popc(b & lt_mask)] = (uint16_t)en;
+        }
         nq += __popc(b);
       }
-      if (lane < ITEMS) wdrop[warp][lane] = 0;
       __syncwarp();
       for (uint32_t e = lane; e < nq; e += 32) {
         const uint32_t en = q[e];
-        const int qr = (int)(en >> 9) & 3, k = (int)(en >> 5) & 15, l = (int)(en & 31);
-        const P p = *reinterpret_cast<const P*>(base + (k * kThreads + warp * 32 + l) * PB);
+        const int k = (int)(en >> 5) & 15, l = (int)(en & 31);
+        const P p = *reinterpret_cast<const P*>(base + (wb + k * 32 + l) * PB);
         float X, Y;
         f32_view<DT>(p, X, Y);
-        const int b = stair_bucket(sort_u(X, Y, qr), slo[qr], ssc[qr]);
-        if (cmp_key_hi<DT>(p, qr) > __ldg(pre + qr * kStairB + b)) atomicOr(&wdrop[warp][k], 1u << l);
+        uint32_t r;
+        if constexpr (DT == DT_F64) {
+          const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
+          const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
+          const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
+          const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
+          // first edge not certainly inside decides: outside -> region,
+          // undecided -> exact test
+          r = !(d3 > cp.fE[3]) ? (d3 < -cp.fE[3] ? 4u : 15u) : 0u;
+          r = !(d2 > cp.fE[2]) ? (d2 < -cp.fE[2] ? 3u : 15u) : r;
+          r = !(d1 > cp.fE[1]) ? (d1 < -cp.fE[1] ? 2u : 15u) : r;
+          r = !(d0 > cp.fE[0]) ? (d0 < -cp.fE[0] ? 1u : 15u) : r;
+          if (r == 15u) r = (uint32_t)region_exact_f64(p.x, p.y, cg.ex, cg.ey, cp.flags);
+        } else {
+          r = (en >> 9) & 0xFu;
+          if (r == 15u) r = (uint32_t)region_exact_i32_wide(p.x, p.y, cg.ex, cg.ey, cp.flags);
+        }
+        if (r != 0 && (cp.flags & SF_STAIRS)) {
+          const int qr = (int)r - 1;
+          const int b = stair_bucket(sort_u(X, Y, qr), wp.slo[qr], wp.ssc[qr]);
+          if (cmp_key_hi<DT>(p, qr) > __ldg(pre + qr * kStairB + b)) r = 0;    // dominated
+        }
+        rk[k * 32 + l] = (uint8_t)r;
       }
       __syncwarp();
 #pragma unroll
-      for (int k = 0; k < ITEMS; k++)
-        if ((wdrop[warp][k] >> lane) & 1u) regs &= ~(0xFull << (4 * k));      // dominated
+      for (int k = 0; k < IW; k++)
+        if ((nim >> k) & 1u) regs |= (uint64_t)rk[k * 32 + lane] << (4 * k);
     }
+    // warp-local stable compaction into the warp's sub-slot of the tile
+    uint32_t rc[4] = {0, 0, 0, 0};
+    if (__any_sync(0xFFFFFFFFu, regs != 0)) {
+      const int64_t ob = sd.off + t0 + wb;
+      uint32_t run = 0;
 #pragma unroll
-    for (int k = 0; k < ITEMS; k++) {
-      const uint32_t b = __ballot_sync(0xFFFFFFFFu, ((regs >> (4 * k)) & 0xFull) != 0);
-      if (lane == 0) { cnt[k][warp] = __popc(b); bal[k][warp] = b; }
-    }
-    __syncthreads();
-    // exclusive scan over (item, warp) in point order: positions within the
-    // tile's own slot range; per-region counts of the tile
-    if (warp == 0) {
-      constexpr int per = ITEMS * kWarps / 32;
-      uint32_t loc[per];
-      uint32_t sum = 0;
-#pragma unroll
-      for (int q = 0; q < per; q++) {
-        int f = lane * per + q;
-        loc[q] = cnt[f / kWarps][f % kWarps];
-        sum += loc[q];
-      }
-      uint32_t x = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += y;
-      }
-      uint32_t run = x - sum;
-#pragma unroll
-      for (int q = 0; q < per; q++) {
-        int f = lane * per + q;
-        cnt[f / kWarps][f % kWarps] = run;
-        run += loc[q];
-      }
-      if (lane < 4) rcnt[lane] = 0;
-    }
-    __syncthreads();
-    if (regs) {
-      uint64_t* keys = w.keyB + sd.off + t0;
-      uint32_t* vals = w.valB + sd.off + t0;
-      uint64_t* spv = w.spvB + sd.off + t0;
-      const uint32_t lt_mask = (1u << lane) - 1u;
-#pragma unroll
-      for (int k = 0; k < ITEMS; k++) {
-        const int r = (int)((regs >> (4 * k)) & 0xF);
+      for (int k = 0; k < IW; k++) {
+        const int r = (int)((regs >> (4 * k)) & 0xFull);
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
         if (r != 0) {
-          const uint32_t b = bal[k][warp];
-          const int i = k * kThreads + tid;
-          const P p = *reinterpret_cast<const P*>(base + (size_t)i * PB);
-          const uint32_t pos = cnt[k][warp] + __popc(b & lt_mask);
-          keys[pos] = sort_key<DT>(p, r);
-          vals[pos] = ((uint32_t)(r - 1) << 30) | (uint32_t)(t0 + i);
-          if constexpr (DT == DT_F64) spv[pos] = spa_v_f64(p.x, p.y, r - 1);
-          else spv[pos] = spa_v_i32(p.x, p.y, r - 1);
-          atomicAdd(&rcnt[r - 1], 1u);
+          const int i = wb + k * 32 + lane;
+          const P p = *reinterpret_cast<const P*>(base + i * PB);
+          const int64_t o = ob + run + __popc(b & lt_mask);
+          w.keyB[o] = sort_key<DT>(p, r);
+          w.valB[o] = ((uint32_t)(r - 1) << 30) | (uint32_t)(t0 + i);
+          if constexpr (DT == DT_F64) w.spvB[o] = spa_v_f64(p.x, p.y, r - 1);
+          else w.spvB[o] = spa_v_i32(p.x, p.y, r - 1);
+          rc[r - 1]++;
         }
+        run += __popc(b);
       }
+#pragma unroll
+      for (int q = 0; q < 4; q++) rc[q] = __reduce_add_sync(0xFFFFFFFFu, rc[q]);
     }
-    __syncthreads();                     // slot and st_tile[slot] free again
-    if (tid == 0) {
-      w.tcnt[tile] = (uint64_t)rcnt[0] | ((uint64_t)rcnt[1] << 16) | ((uint64_t)rcnt[2] << 32) |
-                     ((uint64_t)rcnt[3] << 48);
+    __syncwarp();
+    if (lane == 0) {
+      // the warp is done with the stage: release it to the producer
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
+      w.tcnt[(size_t)tile * kClsConsumers + warp] =
+          (uint64_t)rc[0] | ((uint64_t)rc[1] << 16) | ((uint64_t)rc[2] << 32) | ((uint64_t)rc[3] << 48);
       uint32_t* pt = reinterpret_cast<uint32_t*>(w.ptot + sd.chunkP + (int)(lt / kPlanTiles));
       for (int q = 0; q < 4; q++)
-        if (rcnt[q]) atomicAdd(pt + q, rcnt[q]);
-      fence_async_smem();
-      issue(slot);
+        if (rc[q]) atomicAdd(pt + q, rc[q]);
     }
   }
 }
 
 // ------------------------------------------------------------ gather plan
 //
-// After a2 every tile holds its survivors (index order, regions mixed) at the
-// start of its own slot range, and its per-region counts in tcnt.  k_plan
-// gives every tile its per-region exclusive offset within the set (toff) and
+// After a2 every (tile, consumer warp) sub-slot holds its survivors (index
+// order, regions mixed) and its per-region counts in tcnt.  k_plan gives
+// every sub-slot its per-region exclusive offset within the set (toff) and
 // every set its region totals; its last CTA decides per set between the
 // shared-memory path (all regions <= kSmallMax) and the multi-CTA sort, and
 // plans both.  k_gather then moves the records into region-major order.
@@ -911,15 +914,16 @@ __global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
     carry[threadIdx.x] = b;
   }
   __syncthreads();
-  constexpr int per = kPlanTiles / kThreads;
-  const int t0 = lc * kPlanTiles + threadIdx.x * per;     // set-local tiles of this thread
-  uint32_t v[per][4], own[4] = {0, 0, 0, 0};
-#pragma unroll
+  constexpr int per = kPlanTiles * kClsConsumers / kThreads;      // sub-slots per thread
+  const int64_t nslot = (int64_t)sd.ntile2 * kClsConsumers;
+  const int64_t s0 = (int64_t)lc * kPlanTiles * kClsConsumers + threadIdx.x * per;
+  const uint64_t* tc = w.tcnt + (size_t)sd.tile2 * kClsConsumers;
+  uint32_t own[4] = {0, 0, 0, 0};
   for (int q = 0; q < per; q++) {
-    const int t = t0 + q;
-    const uint64_t c = t < sd.ntile2 ? w.tcnt[sd.tile2 + t] : 0ull;
+    const int64_t t = s0 + q;
+    const uint64_t c = t < nslot ? tc[t] : 0ull;
 #pragma unroll
-    for (int r = 0; r < 4; r++) { v[q][r] = (uint32_t)(c >> (16 * r)) & 0xFFFFu; own[r] += v[q][r]; }
+    for (int r = 0; r < 4; r++) own[r] += (uint32_t)(c >> (16 * r)) & 0xFFFFu;
   }
   uint32_t x[4];
 #pragma unroll
@@ -941,15 +945,17 @@ __global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
     run[r] = carry[r] + x[r] - own[r];
     for (int q = 0; q < warp; q++) run[r] += wsum[r][q];
   }
-#pragma unroll
+  uint4* to = w.toff + (size_t)sd.tile2 * kClsConsumers;
   for (int q = 0; q < per; q++) {
-    const int t = t0 + q;
-    if (t < sd.ntile2) w.toff[sd.tile2 + t] = make_uint4(run[0], run[1], run[2], run[3]);
+    const int64_t t = s0 + q;
+    if (t >= nslot) break;
+    const uint64_t c = tc[t];
+    if (c) to[t] = make_uint4(run[0], run[1], run[2], run[3]);
 #pragma unroll
-    for (int r = 0; r < 4; r++) run[r] += v[q][r];
+    for (int r = 0; r < 4; r++) run[r] += (uint32_t)(c >> (16 * r)) & 0xFFFFu;
   }
   if (lc == sd.nchunkP - 1 && threadIdx.x == kThreads - 1) {
-    // the set's last chunk: run[] now holds the set's totals
+    // the set's last chunk: run[] holds the set's totals
     SetCtl& c = w.ctl[s];
     uint32_t s1 = 0;
     bool big = false;
@@ -973,62 +979,71 @@ __global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
   plan_sort(j, w);
   if (threadIdx.x == 0) {
     uint32_t k = 0;
-    for (int s = 0; s < j.nsets; s++) {
-      const SetCtl& c = w.ctl[s];
+    for (int s2 = 0; s2 < j.nsets; s2++) {
+      const SetCtl& c = w.ctl[s2];
       if (c.status != 0 || (c.flags & SF_BIG)) continue;
       for (int r = 0; r < 4; r++)
-        if (c.cnt[r]) w.small_seg[k++] = (uint32_t)(4 * s + r);
+        if (c.cnt[r]) w.small_seg[k++] = (uint32_t)(4 * s2 + r);
     }
     w.ctr[CT_SMALL_TOTAL] = k;
   }
 }
 
-// One warp per a2 tile: stable move of the tile's survivors to their
-// region-major positions in the set's record stream.
+// One warp per group of 32 sub-slots: stable move of each non-empty
+// sub-slot's survivors to their region-major positions in the set's stream.
 __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int nw = gridDim.x * kWarps;
-  for (int t = blockIdx.x * kWarps + (threadIdx.x >> 5); t < j.ntile2; t += nw) {
-    const uint64_t tc = w.tcnt[t];
-    if (tc == 0) continue;
-    int s = 0;
-    if (j.sets) {
-      int lo = 0, hi = j.nsets - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (j.sets[mid].tile2 <= t) lo = mid; else hi = mid - 1;
-      }
-      s = lo;
-    }
-    const SetDesc sd = get_set(j, s);
-    const SetCtl& c = w.ctl[s];
-    const uint4 of = w.toff[t];
-    uint32_t base[4];
-    base[0] = of.x;
-    base[1] = c.cnt[0] + of.y;
-    base[2] = c.cnt[0] + c.cnt[1] + of.z;
-    base[3] = c.cnt[0] + c.cnt[1] + c.cnt[2] + of.w;
-    const uint32_t n = (uint32_t)(tc & 0xFFFFu) + (uint32_t)((tc >> 16) & 0xFFFFu) +
-                       (uint32_t)((tc >> 32) & 0xFFFFu) + (uint32_t)(tc >> 48);
-    const int64_t src = sd.off + (int64_t)(t - sd.tile2) * cls_tile(j.dtype);
-    for (uint32_t i0 = 0; i0 < n; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      const bool ok = i < n;
-      const uint64_t key = ok ? w.keyB[src + i] : 0;
-      const uint32_t val = ok ? w.valB[src + i] : 0;
-      const uint64_t spv = ok ? w.spvB[src + i] : 0;
-      const int r = ok ? (int)(val >> 30) : -1;
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, r == q);
-        if (r == q) {
-          const uint32_t pos = base[q] + __popc(b & lt_mask);
-          w.keyA[sd.off + pos] = key;
-          w.valA[sd.off + pos] = val;
-          w.spvA[sd.off + pos] = spv;
+  const int64_t nslots = (int64_t)j.ntile2 * kClsConsumers;
+  const int tile_pts = cls_tile(j.dtype), sub = tile_pts / kClsConsumers;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  for (int64_t g0 = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * 32; g0 < nslots; g0 += nw * 32) {
+    const uint64_t mine = g0 + lane < nslots ? w.tcnt[g0 + lane] : 0ull;
+    uint32_t busy = __ballot_sync(0xFFFFFFFFu, mine != 0);
+    while (busy) {
+      const int l = __ffs(busy) - 1;
+      busy &= busy - 1;
+      const int64_t slot = g0 + l;
+      const uint64_t tc = __shfl_sync(0xFFFFFFFFu, mine, l);
+      const int tile = (int)(slot / kClsConsumers), cw = (int)(slot % kClsConsumers);
+      int s = 0;
+      if (j.sets) {
+        int lo = 0, hi = j.nsets - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (j.sets[mid].tile2 <= tile) lo = mid; else hi = mid - 1;
         }
-        base[q] += __popc(b);
+        s = lo;
+      }
+      const SetDesc sd = get_set(j, s);
+      const SetCtl& c = w.ctl[s];
+      const uint4 of = w.toff[slot];
+      uint32_t base[4];
+      base[0] = of.x;
+      base[1] = c.cnt[0] + of.y;
+      base[2] = c.cnt[0] + c.cnt[1] + of.z;
+      base[3] = c.cnt[0] + c.cnt[1] + c.cnt[2] + of.w;
+      const uint32_t n = (uint32_t)(tc & 0xFFFFu) + (uint32_t)((tc >> 16) & 0xFFFFu) +
+                         (uint32_t)((tc >> 32) & 0xFFFFu) + (uint32_t)(tc >> 48);
+      const int64_t src = sd.off + (int64_t)(tile - sd.tile2) * tile_pts + (int64_t)cw * sub;
+      for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const bool ok = i < n;
+        const uint64_t key = ok ? w.keyB[src + i] : 0;
+        const uint32_t val = ok ? w.valB[src + i] : 0;
+        const uint64_t spv = ok ? w.spvB[src + i] : 0;
+        const int r = ok ? (int)(val >> 30) : -1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const uint32_t b = __ballot_sync(0xFFFFFFFFu, r == q);
+          if (r == q) {
+            const uint32_t pos = base[q] + __popc(b & lt_mask);
+            w.keyA[sd.off + pos] = key;
+            w.valA[sd.off + pos] = val;
+            w.spvA[sd.off + pos] = spv;
+          }
+          base[q] += __popc(b);
+        }
       }
     }
   }
@@ -1057,7 +1072,7 @@ int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
 
 int launch_gather(const Job& j, const Ws& w, const Launch& L) {
   k_plan<<<j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream>>>(j, w);
-  int gg = (j.ntile2 + kWarps - 1) / kWarps;
+  int gg = (int)(((int64_t)j.ntile2 * kClsConsumers + 32 * kWarps - 1) / (32 * kWarps));
   if (gg > L.grid_cap) gg = L.grid_cap;
   if (gg < 1) gg = 1;
   k_gather<<<gg, kThreads, 0, L.stream>>>(j, w);
@@ -1073,14 +1088,14 @@ int launch_classify(const Job& j, const Ws& w, const Launch& L) {
       return true;
     }();
     (void)once;
-    k_classify<DT_F64><<<grid, kThreads, cls_smem_bytes<DT_F64>(), L.stream>>>(j, w);
+    k_classify<DT_F64><<<grid, kClsBlock, cls_smem_bytes<DT_F64>(), L.stream>>>(j, w);
   } else {
     static bool once = [] {
       cudaFuncSetAttribute(k_classify<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT_I32>());
       return true;
     }();
     (void)once;
-    k_classify<DT_I32><<<grid, kThreads, cls_smem_bytes<DT_I32>(), L.stream>>>(j, w);
+    k_classify<DT_I32><<<grid, kClsBlock, cls_smem_bytes<DT_I32>(), L.stream>>>(j, w);
   }
   return 1;
 }
