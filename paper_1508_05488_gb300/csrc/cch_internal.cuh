@@ -39,7 +39,7 @@ constexpr int kThreads = 256;          // every kernel runs 256-thread CTAs
 constexpr int kWarps = kThreads / 32;
 // a2 tiles are 32 KB of points: 2048 float64 or 4096 int32 points
 constexpr int kClsTileBytes = 32768;
-constexpr int kClsStages = 3;          // TMA ring depth of a2
+constexpr int kClsStages = 2;          // TMA ring depth of a2
 __host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048 : 4096; }
 // SPA-dominance prefilter ("stairs"): per region, the prefix minimum of the
 // compared coordinate over buckets of the sort coordinate, built from a
@@ -152,6 +152,7 @@ struct Part {
 // Device-resident per-set state (zeroed every call).
 struct SetCtl {
   uint64_t ek1[4], ek2[4];   // a1 lexicographic keys of E1..E4
+  uint64_t dq[4];            // dominance points: ~(score key << 32 | index), largest wins
   double   ex[4], ey[4];     // E1..E4 coordinates (int32 widened exactly)
   float    fA[4], fB[4], fC[4], fE[4];   // FP32 filter of edge k (f64 only)
   uint32_t eidx[4];          // set-local indices of E1..E4
@@ -162,6 +163,7 @@ struct SetCtl {
   uint32_t cnt[4];           // records per region
   uint32_t s2[4];            // SPA survivors per region
   float    slo[4], shi[4], sscale[4];  // stairs bucket map of region r: b = (u - lo) * scale
+  float    bx0, bx1, by0, by1;          // dominance box (FP32 views, open; empty when zero)
   uint32_t arrive3;          // stairs chunk arrivals
   uint32_t pad1;
 };

@@ -160,6 +160,12 @@ __device__ __forceinline__ int stair_bucket(float u, float lo, float scale) {
   return min(max(b, 0), kStairB - 1);
 }
 
+// Order-preserving unsigned key of a (non-NaN) float.
+__device__ __forceinline__ uint32_t f32_order(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 // FP32 view of a point used by the filter and the stairs (truncated float64,
 // rounded int32): monotone in each coordinate.
 template <int DT>
@@ -454,6 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   const int64_t c0 = sd.n - m + (int64_t)(chunk - sd.chunk3) * kStairChunk;
   const int64_t c1 = min(sd.n, c0 + kStairChunk);
   const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
+  uint64_t dq[4] = {~0ull, ~0ull, ~0ull, ~0ull};   // best score key << 32 | index per quadrant
   constexpr int U = 8;
   for (int64_t b0 = c0; b0 < c1; b0 += (int64_t)kThreads * U) {
     P v[U];
@@ -468,6 +475,12 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
       if (i >= c1) continue;
       float X, Y;
       f32_view<DT>(v[u], X, Y);
+      // quadrant scores: lower-left x+y, lower-right y-x, upper-right -x-y,
+      // upper-left x-y (smaller is further into the quadrant)
+      dq[0] = min(dq[0], ((uint64_t)f32_order(__fadd_rn(X, Y)) << 32) | (uint32_t)i);
+      dq[1] = min(dq[1], ((uint64_t)f32_order(__fsub_rn(Y, X)) << 32) | (uint32_t)i);
+      dq[2] = min(dq[2], ((uint64_t)f32_order(-__fadd_rn(X, Y)) << 32) | (uint32_t)i);
+      dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | (uint32_t)i);
 #pragma unroll
       for (int r = 0; r < 4; r++) {
         float su = sort_u(X, Y, r);
@@ -475,6 +488,13 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
           atomicMin(&tb[r][stair_bucket(su, lo[r], sc[r])], cmp_key_hi<DT>(v[u], r));
       }
     }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dq[q] = min(dq[q], __shfl_xor_sync(0xFFFFFFFFu, dq[q], o));
+    if ((threadIdx.x & 31) == 0 && dq[q] != ~0ull)
+      atomicMax((unsigned long long*)&w.ctl[s].dq[q], (unsigned long long)~dq[q]);
   }
   __syncthreads();
   uint32_t* g = w.stairs + (size_t)s * 4 * kStairB;
@@ -490,6 +510,22 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // dominance box: a point strictly inside it is strictly beaten in all four
+  // quadrants by sample points (Qll lower-left of it, Qlr lower-right, ...)
+  if (threadIdx.x == 0) {
+    const uint64_t d0 = *(volatile uint64_t*)&c.dq[0], d1 = *(volatile uint64_t*)&c.dq[1];
+    const uint64_t d2 = *(volatile uint64_t*)&c.dq[2], d3 = *(volatile uint64_t*)&c.dq[3];
+    if (d0 && d1 && d2 && d3) {
+      float X[4], Y[4];
+      const uint64_t d[4] = {d0, d1, d2, d3};
+      for (int q = 0; q < 4; q++) f32_view<DT>(pts[(uint32_t)~d[q]], X[q], Y[q]);
+      SetCtl& cw = w.ctl[s];
+      cw.bx0 = fmaxf(X[0], X[3]);
+      cw.bx1 = fminf(X[1], X[2]);
+      cw.by0 = fmaxf(Y[0], Y[1]);
+      cw.by1 = fminf(Y[2], Y[3]);
+    }
+  }
   // exclusive prefix minimum per region, seeded with the first extreme
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 4) {
@@ -618,6 +654,7 @@ constexpr int cls_smem_bytes() {
 // the rest lives in the warp's shared-memory copy (WarpParams).
 struct ClsParams {
   float fA[4], fB[4], fC[4], fE[4];
+  float bx0, bx1, by0, by1;           // dominance box (empty: never inside)
   uint32_t flags;
   int32_t status;
 };
@@ -741,6 +778,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
         wp.ix[lane] = (int)c.ex[lane]; wp.iy[lane] = (int)c.ey[lane];
       }
       __syncwarp();
+      cp.bx0 = c.bx0; cp.bx1 = c.bx1; cp.by0 = c.by0; cp.by1 = c.by1;
       cp.flags = c.flags;
       cp.status = c.status;
       cur_set = s;
@@ -770,7 +808,8 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
           const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
           const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
           const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
-          const bool in = (d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3]);
+          const bool in = ((d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3])) |
+                          ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1));
           nim |= (uint32_t)(!in) << k;
         } else {
           uint32_t r = 0;
@@ -784,6 +823,8 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
                 r = (uint32_t)q + 1;
             }
           }
+          const float X = __int2float_rn(p.x), Y = __int2float_rn(p.y);
+          if ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1)) r = 0;
           ireg[k >> 3] |= r << (4 * (k & 7));
           nim |= (uint32_t)(r != 0) << k;
         }

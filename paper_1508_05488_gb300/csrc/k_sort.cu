@@ -65,6 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Job j, Ws w) {
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31;
   const uint32_t total = w.ctr[CT_SORT_TOTAL];
+  if (total == 0) {          // no multi-block set: one CTA plans, no arrival count
+    if (blockIdx.x == 0) plan_spa(j, w);
+    return;
+  }
   const int npass_key = j.dtype == DT_F64 ? 8 : 4;   // int32 keys have 4 zero bytes
   for (uint32_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
     const int s = seg_of(w.sort_start, j.nsets, tile);
@@ -123,6 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(Job j, Ws w, int p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t total = w.ctr[CT_SORT_TOTAL];
+  if (total == 0) return;
   const uint32_t tag = (j.epoch << 4) | (uint32_t)p;
 
   for (;;) {

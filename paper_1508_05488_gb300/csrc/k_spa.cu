@@ -110,6 +110,10 @@ __global__ void __launch_bounds__(kThreads) k_spa(Job j, Ws w) {
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = w.ctr[CT_SPA_TOTAL];
+  if (total == 0) {          // no multi-block set: one CTA plans the chains
+    if (blockIdx.x == 0) plan_chain(j, w);
+    return;
+  }
   const uint32_t tag_min = (j.epoch << 4) | 10u, tag_cnt = (j.epoch << 4) | 11u;
   const P* pts_all = reinterpret_cast<const P*>(j.pts);
 
