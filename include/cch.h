@@ -131,14 +131,14 @@ int cch_hull_stages(const void *points, int64_t n, int dtype, uint32_t opts,
 
 /*
  * Stage timing.  cch_profile(1) makes every later call record CUDA events on
- * its stream around eight stages: (0) the extremes pass a1, (1) the
+ * its stream around seven stages: (0) the extremes pass a1, (1) the
  * dominance-table sample, (2) the classify pass a2, (3) the gather of the
  * survivors into region order, (4) sort and SPA of the shared-memory path,
- * (5) sort and (6) SPA of the multi-block path, (7) chain hull and output.
+ * (5) sort and SPA of the multi-block path, (6) chain hull and output.
  * cch_profile_read synchronises on the recorded events, writes the summed
- * milliseconds per stage to stage_ms[0 .. min(8, max_stages)), the number of
+ * milliseconds per stage to stage_ms[0 .. min(7, max_stages)), the number of
  * calls to *calls (if not NULL), forgets them, and returns the number of
- * stages (8).  cch_profile(0) stops recording.
+ * stages (7).  cch_profile(0) stops recording.
  */
 int cch_profile(int enable);
 int cch_profile_read(double *stage_ms, int max_stages, int64_t *calls);

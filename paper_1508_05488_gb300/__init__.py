@@ -245,7 +245,7 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None
     }
 
 
-STAGE_NAMES = ("k_extremes", "k_stairs", "k_classify", "gather", "small", "sort", "spa", "chain")
+STAGE_NAMES = ("k_extremes", "k_stairs", "k_classify", "gather", "small", "big", "chain")
 
 
 def profile(enable: bool = True):

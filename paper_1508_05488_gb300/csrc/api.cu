@@ -112,7 +112,7 @@ std::atomic<uint64_t> g_launches{0};
 
 // Optional stage timing: CUDA events around the stages of every call, read
 // back (and summed) by cch_profile_read.
-constexpr int kStages = 8;   // a1, stairs, a2, gather, small path, big sort, big SPA, chain
+constexpr int kStages = 7;   // a1, stairs, a2, gather, small path, multi-block path, chain
 struct ProfRec { cudaEvent_t ev[kStages + 1]; };
 bool g_prof = false;
 std::vector<ProfRec> g_prof_pending, g_prof_free;
@@ -233,13 +233,11 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
   if (ev) cudaEventRecord(ev[4], stream);
   nk += launch_small(j, L.w, La);
   if (ev) cudaEventRecord(ev[5], stream);
-  nk += launch_sort(j, L.w, La);
+  nk += launch_big(j, L.w, La);
   if (ev) cudaEventRecord(ev[6], stream);
-  nk += launch_spa(j, L.w, La);
-  if (ev) cudaEventRecord(ev[7], stream);
   nk += launch_chain(j, L.w, La);
   if (stages) { launch_extract_spa(j, L.w, stages->spa_idx, stream); nk++; }
-  if (ev) { cudaEventRecord(ev[8], stream); g_prof_pending.push_back(rec); }
+  if (ev) { cudaEventRecord(ev[7], stream); g_prof_pending.push_back(rec); }
   g_launches += (uint64_t)nk;
   if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
   if (ws_out) *ws_out = ws;

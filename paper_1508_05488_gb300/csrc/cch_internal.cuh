@@ -85,9 +85,9 @@ enum : uint32_t {
 // dynamic-tile and done counters (zeroed every call)
 enum : int {
   CT_CLS_TILE = 0, CT_CLS_DONE, CT_PLAN_DONE, CT_SMALL_TOTAL,
-  CT_HIST_TILE, CT_HIST_DONE,
+  CT_BIG_BAR,                          // grid barrier arrivals of the multi-block kernel
   CT_SORT_TILE0,                       // + pass
-  CT_SPA_TILE = CT_SORT_TILE0 + kSortPasses, CT_SPA_DONE,
+  CT_SPA_TILE = CT_SORT_TILE0 + kSortPasses,
   CT_OUT_TILE, CT_OUT_DONE,
   CT_SORT_TOTAL,                       // plan results
   CT_SPA_TOTAL,
@@ -543,8 +543,7 @@ int launch_stairs(const Job& j, const Ws& w, const Launch& L);
 int launch_classify(const Job& j, const Ws& w, const Launch& L);
 int launch_gather(const Job& j, const Ws& w, const Launch& L);
 int launch_small(const Job& j, const Ws& w, const Launch& L);
-int launch_sort(const Job& j, const Ws& w, const Launch& L);
-int launch_spa(const Job& j, const Ws& w, const Launch& L);
+int launch_big(const Job& j, const Ws& w, const Launch& L);
 int launch_chain(const Job& j, const Ws& w, const Launch& L);
 // stage extraction (cch_hull_stages)
 void launch_extract_r1(const Job& j, const Ws& w, int32_t* r1_idx, int32_t* r1_region, cudaStream_t st);

@@ -165,8 +165,7 @@ extern "C" int cch_hull_noalloc(const void* points, int64_t n, int dtype, int32_
   launch_classify(j, w, L);
   launch_gather(j, w, L);
   launch_small(j, w, L);
-  launch_sort(j, w, L);
-  launch_spa(j, w, L);
+  launch_big(j, w, L);
   launch_chain(j, w, L);
   if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
   return CCH_OK;
