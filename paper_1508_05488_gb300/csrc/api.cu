@@ -64,7 +64,6 @@ Layout layout(const Dims& d, char* base) {
   L.status_bytes = o - L.status_off;
   L.w.part = (Part*)take(sizeof(Part) * (size_t)std::max(d.nchunk1, 1));
   L.w.tcnt = (uint64_t*)take(8 * 8 * (size_t)std::max(d.ntile2, 1));
-  L.w.toff = (uint4*)take(16 * 8 * (size_t)std::max(d.ntile2, 1));
   L.w.small_seg = (uint32_t*)take(4 * 4 * (size_t)d.nsets);
   L.w.keyA = (uint64_t*)take(8 * (size_t)d.N);
   L.w.keyB = (uint64_t*)take(8 * (size_t)d.N);
@@ -217,6 +216,7 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
     cudaEventRecord(ws->sets_done, stream);
     j.sets = dsets;
   }
+  if (stages) { j.r1_idx = stages->r1_idx; j.r1_region = stages->r1_region; }
   Launch La{stream, grid_cap(), 2 * sm_count()};
   ProfRec rec{};
   cudaEvent_t* ev = prof_begin(rec);
@@ -229,7 +229,6 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
   nk += launch_classify(j, L.w, La);
   if (ev) cudaEventRecord(ev[3], stream);
   nk += launch_gather(j, L.w, La);
-  if (stages) { launch_extract_r1(j, L.w, stages->r1_idx, stages->r1_region, stream); nk++; }
   if (ev) cudaEventRecord(ev[4], stream);
   nk += launch_small(j, L.w, La);
   if (ev) cudaEventRecord(ev[5], stream);

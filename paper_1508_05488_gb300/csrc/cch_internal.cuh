@@ -40,6 +40,7 @@ constexpr int kWarps = kThreads / 32;
 // a2 tiles are 32 KB of points: 2048 float64 or 4096 int32 points
 constexpr int kClsTileBytes = 32768;
 constexpr int kClsStages = 2;          // TMA ring depth of a2
+constexpr int kClsConsumers = 8;       // consumer warps of a2: each tile has 8 sub-slots
 __host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048 : 4096; }
 // SPA-dominance prefilter ("stairs"): per region, the prefix minimum of the
 // compared coordinate over buckets of the sort coordinate, built from a
@@ -47,7 +48,7 @@ __host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048
 constexpr int kStairB = 1024;          // buckets per region
 constexpr int64_t kStairSample = int64_t(1) << 20;   // sample points per set (the last ones)
 constexpr int kStairChunk = 8192;      // sample points per CTA
-constexpr int kPlanTiles = 1024;       // a2 tiles per gather-plan CTA
+constexpr int kPlanTiles = 64;         // a2 tiles per survivor-count chunk (one gather CTA)
 // Sample of a set: its last m points (the most recently streamed by a1),
 // m = min(n, 2^20, max(8192, n / 16)).
 __host__ __device__ inline int64_t stairs_sample(int64_t n) {
@@ -84,7 +85,7 @@ enum : uint32_t {
 
 // dynamic-tile and done counters (zeroed every call)
 enum : int {
-  CT_CLS_TILE = 0, CT_CLS_DONE, CT_PLAN_DONE, CT_SMALL_TOTAL,
+  CT_CLS_TILE = 0, CT_PLAN_DONE, CT_SMALL_TOTAL,
   CT_BIG_BAR,                          // grid barrier arrivals of the multi-block kernel
   CT_SORT_TILE0,                       // + pass
   CT_SPA_TILE = CT_SORT_TILE0 + kSortPasses,
@@ -108,8 +109,8 @@ struct SetDesc {
   int32_t ntile2;       // a2 tiles of this set
   int32_t chunk3;       // first stairs chunk
   int32_t nchunk3;      // stairs chunks of this set
-  int32_t chunkP;       // first gather-plan chunk (kPlanTiles a2 tiles each)
-  int32_t nchunkP;      // gather-plan chunks of this set
+  int32_t chunkP;       // first survivor-count chunk (kPlanTiles a2 tiles each)
+  int32_t nchunkP;      // survivor-count chunks of this set
 };
 
 // Per-call launch description.  A single hull carries its descriptor inline;
@@ -122,7 +123,7 @@ struct Job {
   int32_t nchunk1;      // total a1 chunks
   int32_t ntile2;       // total a2 tiles
   int32_t nchunk3;      // total stairs chunks
-  int32_t nchunkP;      // total gather-plan chunks
+  int32_t nchunkP;      // total survivor-count chunks
   int64_t chunk1_len;   // a1 chunk length (points), multiple of 256
   uint32_t epoch;       // look-back flag epoch of this call (1..0xFFFF)
   uint32_t opts;        // OPT_* bits
@@ -130,6 +131,8 @@ struct Job {
   SetDesc one;
   int32_t* out_idx;     // device
   int32_t* out_counts;  // device, [nsets]
+  int32_t* r1_idx;      // stage hook (set 0, or nullptr): round-1 survivors, region-major
+  int32_t* r1_region;   //   and their regions 1..4
 };
 
 enum : uint32_t {
@@ -182,9 +185,8 @@ struct Ws {
   SetCtl* ctl;               // [nsets]
   uint32_t* ctr;             // [CT_COUNT]
   Part* part;                // [nchunk1]
-  uint4* ptot;               // [nchunkP] survivors per region of a gather-plan chunk (cleared per call)
-  uint64_t* tcnt;            // [ntile2] survivors of an a2 tile per region (4 x u16)
-  uint4* toff;               // [ntile2] exclusive prefix of tcnt over the set's tiles
+  uint4* ptot;               // [nchunkP] survivors per region of a survivor-count chunk (cleared per call)
+  uint64_t* tcnt;            // [ntile2 * kClsConsumers] survivors of an a2 sub-slot per region (4 x u16)
   uint32_t* small_seg;       // [4 nsets] (set, region) segments of the shared-memory path
   uint64_t* keyA; uint32_t* valA;     // [N] records (sort ping)
   uint64_t* keyB; uint32_t* valB;     // [N] records (sort pong)
@@ -205,6 +207,12 @@ struct Ws {
   uint64_t* st_out;          // [max_out_tiles]
   uint32_t* stairs;          // [nsets][4][kStairB] bucket minima, then prefix minima
 };
+
+// Chain slots of (set s, region r) when the region's records start at `rbase`
+// within the set (the sum of the earlier regions' counts).
+__device__ __forceinline__ int64_t chain_base_at(const SetDesc& sd, int s, int r, uint32_t rbase) {
+  return sd.off + 8 * (int64_t)s + 2 * r + rbase;
+}
 
 // Chain slots of (set s, region r): base + position, positions 0 .. L-1 with
 // position 0 = E_r, L-1 = E_{r+1}, 1 .. L-2 the SPA survivors in order.
@@ -529,6 +537,125 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// ------------------------------------------------- round-1 survivor moves
+// a2 leaves the survivors of every (tile, consumer warp) sub-slot in place:
+// sub-slot g of a set (g = local tile * kClsConsumers + warp) holds
+// sum(tcnt[g]) records in index order, regions mixed, at
+// sd.off + g * (tile points / kClsConsumers) of keyB / valB / spvB.  Chunk c
+// of a set is sub-slots [c, c + 1) * kPlanTiles * kClsConsumers; ptot holds
+// its per-region totals.
+
+// Warp-cooperative, order-preserving move of the region-`rsel` survivors
+// (rsel < 0: all regions) of sub-slots [g0, g1) of set s to their
+// region-major records: region q's next survivor goes to record
+// sd.off + roff[q] + pos[q], and pos[q] advances.  pos and roff are the same
+// in every lane.  With the stage hook set (set 0 only) the moved survivors
+// are also listed in j.r1_idx / j.r1_region.
+__device__ __forceinline__ void move_subslots(const Job& j, const Ws& w, const SetDesc& sd, int s,
+                                              int64_t g0, int64_t g1, int rsel, uint32_t pos[4],
+                                              const uint32_t roff[4]) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int sub = cls_tile(j.dtype) / kClsConsumers;
+  const uint64_t* tc = w.tcnt + (size_t)sd.tile2 * kClsConsumers;
+  const bool hook = j.r1_idx != nullptr && s == 0;
+  for (int64_t gs = g0; gs < g1; gs += 32) {
+    const int64_t g = gs + lane;
+    const uint64_t mine = g < g1 ? tc[g] : 0ull;
+    uint32_t pre[4], tot[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t c = (uint32_t)(mine >> (16 * q)) & 0xFFFFu;
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      pre[q] = x - c;
+      tot[q] = __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+    const uint32_t n = (uint32_t)(mine & 0xFFFFu) + (uint32_t)((mine >> 16) & 0xFFFFu) +
+                       (uint32_t)((mine >> 32) & 0xFFFFu) + (uint32_t)(mine >> 48);
+    const bool want = rsel < 0 ? n != 0 : ((mine >> (16 * rsel)) & 0xFFFFull) != 0;
+    const int64_t src = sd.off + g * sub;
+    if (__reduce_max_sync(0xFFFFFFFFu, want ? n : 0u) <= 8u) {
+      // sparse step: every lane moves its own sub-slot's few records
+      uint32_t b0 = pos[0] + pre[0], b1 = pos[1] + pre[1], b2 = pos[2] + pre[2], b3 = pos[3] + pre[3];
+      const uint32_t nn = want ? n : 0u;
+#pragma unroll 1
+      for (uint32_t i0 = 0; i0 < nn; i0 += 4) {
+        uint32_t val[4];
+        uint64_t key[4], spv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const bool ok = i0 + u < nn;
+          val[u] = ok ? w.valB[src + i0 + u] : 0u;
+          key[u] = ok ? w.keyB[src + i0 + u] : 0ull;
+          spv[u] = ok ? w.spvB[src + i0 + u] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (i0 + u >= nn) continue;
+          const int r = (int)(val[u] >> 30);
+          if (rsel >= 0 && r != rsel) continue;
+          const uint32_t p = r == 0 ? b0 : r == 1 ? b1 : r == 2 ? b2 : b3;
+          const uint32_t ro = r == 0 ? roff[0] : r == 1 ? roff[1] : r == 2 ? roff[2] : roff[3];
+          b0 += r == 0; b1 += r == 1; b2 += r == 2; b3 += r == 3;
+          const int64_t o = sd.off + ro + p;
+          w.keyA[o] = key[u];
+          w.valA[o] = val[u];
+          w.spvA[o] = spv[u];
+          if (hook) {
+            j.r1_idx[ro + p] = (int32_t)(val[u] & kIdxMask);
+            j.r1_region[ro + p] = r + 1;
+          }
+        }
+      }
+    } else {
+      // dense step: the whole warp moves one sub-slot at a time (coalesced)
+      uint32_t busy = __ballot_sync(0xFFFFFFFFu, want);
+      while (busy) {
+        const int l = __ffs(busy) - 1;
+        busy &= busy - 1;
+        uint32_t b[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) b[q] = pos[q] + __shfl_sync(0xFFFFFFFFu, pre[q], l);
+        const uint32_t nl = __shfl_sync(0xFFFFFFFFu, n, l);
+        const int64_t sl = sd.off + (gs + l) * sub;
+        for (uint32_t i0 = 0; i0 < nl; i0 += 32) {
+          const uint32_t i = i0 + lane;
+          const bool ok = i < nl;
+          const uint32_t val = ok ? w.valB[sl + i] : 0u;
+          const int r = ok ? (int)(val >> 30) : -1;
+          const bool mv = rsel < 0 ? ok : r == rsel;
+          const uint64_t key = mv ? w.keyB[sl + i] : 0ull;
+          const uint64_t spv = mv ? w.spvB[sl + i] : 0ull;
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            if (rsel >= 0 && q != rsel) continue;
+            const uint32_t bq = __ballot_sync(0xFFFFFFFFu, mv && r == q);
+            if (mv && r == q) {
+              const uint32_t p = b[q] + __popc(bq & lt_mask);
+              const int64_t o = sd.off + roff[q] + p;
+              w.keyA[o] = key;
+              w.valA[o] = val;
+              w.spvA[o] = spv;
+              if (hook) {
+                j.r1_idx[roff[q] + p] = (int32_t)(val & kIdxMask);
+                j.r1_region[roff[q] + p] = q + 1;
+              }
+            }
+            b[q] += __popc(bq);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) pos[q] += tot[q];
+  }
+}
+
 // ------------------------------------------------------------ launchers
 // (defined in the kernel translation units, called from the API)
 struct Launch {
@@ -546,7 +673,6 @@ int launch_small(const Job& j, const Ws& w, const Launch& L);
 int launch_big(const Job& j, const Ws& w, const Launch& L);
 int launch_chain(const Job& j, const Ws& w, const Launch& L);
 // stage extraction (cch_hull_stages)
-void launch_extract_r1(const Job& j, const Ws& w, int32_t* r1_idx, int32_t* r1_region, cudaStream_t st);
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
 int extremes_blocks_per_sm(int dtype);
 

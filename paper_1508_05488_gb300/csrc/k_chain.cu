@@ -335,15 +335,6 @@ __global__ void __launch_bounds__(kThreads) k_output(Job j, Ws w) {
 }
 
 // ---------------------------------------------------- stage extraction
-__global__ void k_extract_r1(Job j, Ws w, int32_t* r1_idx, int32_t* r1_region) {
-  const uint32_t n1 = w.ctl[0].s1;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
-    uint32_t v = w.valA[i];
-    r1_idx[i] = (int32_t)(v & kIdxMask);
-    r1_region[i] = (int32_t)(v >> 30) + 1;
-  }
-}
-
 __global__ void k_extract_spa(Job j, Ws w, int32_t* spa_idx) {
   const SetDesc sd = get_set(j, 0);
   const SetCtl& c = w.ctl[0];
@@ -355,10 +346,6 @@ __global__ void k_extract_spa(Job j, Ws w, int32_t* spa_idx) {
       spa_idx[o + i] = (int32_t)w.cidx[cb + 1 + i];
     o += m;
   }
-}
-
-void launch_extract_r1(const Job& j, const Ws& w, int32_t* r1_idx, int32_t* r1_region, cudaStream_t st) {
-  k_extract_r1<<<256, kThreads, 0, st>>>(j, w, r1_idx, r1_region);
 }
 
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st) {

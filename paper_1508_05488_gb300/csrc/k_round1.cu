@@ -8,9 +8,11 @@
 //  k_classify  second streaming pass, fed by a TMA ring of shared-memory
 //              tiles: the quadrilateral test with region routing (first k
 //              whose directed edge E_k -> E_{k+1} has the point strictly on
-//              its right, i.e. outside), the dominance prefilter, and stable
-//              compaction of the survivors into one record stream per set
-//              (warp ballots, block scan, decoupled look-back).
+//              its right, i.e. outside) and the dominance prefilters; every
+//              consumer warp compacts the survivors of its part of a tile
+//              (a sub-slot) in place, in index order, and counts them per
+//              region.  The shared-memory path and the multi-block path move
+//              the survivors into region-major order themselves.
 //
 // Dominance prefilter.  SPA (Fig. 2) discards a point P of region R_r when a
 // point Q of R_r before P in the Table 1 order has a strictly better compared
@@ -24,6 +26,14 @@
 // buckets, seeded with the region's first extreme, gives for every bucket a
 // value such that any region point of that bucket with a larger value is
 // dominated by a sample point of a strictly lower bucket.
+//
+// Dominance box.  The same argument in all four quadrants at once: k_stairs
+// also picks the sample point furthest into each quadrant (smallest x+y,
+// y-x, -x-y, x-y).  A point strictly inside the box they span is strictly
+// beaten in every quadrant -- in particular in the quadrant of whichever
+// region it falls in, by a point of that region -- so it is neither a hull
+// vertex nor an SPA survivor.  The test is four FP32 compares on the
+// monotone views.
 #include "cch_internal.cuh"
 
 namespace cch {
@@ -642,7 +652,6 @@ __device__ __forceinline__ uint64_t sort_key(const typename PointT<DT>::T& p, in
   }
 }
 
-constexpr int kClsConsumers = 8;                   // consumer warps of a2
 constexpr int kClsBlock = (kClsConsumers + 1) * 32;  // + one producer warp
 
 template <int DT>
@@ -921,18 +930,20 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
   }
 }
 
-// ------------------------------------------------------------ gather plan
+// ------------------------------------------------------------ gather
 //
-// After a2 every (tile, consumer warp) sub-slot holds its survivors (index
-// order, regions mixed) and its per-region counts in tcnt.  k_plan gives
-// every sub-slot its per-region exclusive offset within the set (toff) and
-// every set its region totals; its last CTA decides per set between the
-// shared-memory path (all regions <= kSmallMax) and the multi-CTA sort, and
-// plans both.  k_gather then moves the records into region-major order.
+// After a2 every (tile, consumer warp) sub-slot holds its survivors in place
+// and a2 has added up every chunk's survivors per region (ptot).  k_gather
+// runs one CTA per chunk: the set's region totals and the chunk's offsets
+// come from ptot, the eight warps split the chunk's sub-slots, and every
+// survivor moves to its region-major record, order kept.  The last CTA to
+// finish decides per set between the shared-memory path (every region at
+// most kSmallMax) and the multi-block sort, and plans both.
 
-__global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
-  __shared__ uint32_t wsum[4][kWarps];
-  __shared__ uint32_t carry[4];
+__global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
+  constexpr int kSubPerWarp = kPlanTiles * kClsConsumers / kWarps;
+  __shared__ uint32_t sh_tot[4], sh_cpre[4];
+  __shared__ uint32_t wtot[kWarps][4];
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int chunk = blockIdx.x;
@@ -947,68 +958,50 @@ __global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
   }
   const SetDesc sd = get_set(j, s);
   const int lc = chunk - sd.chunkP;
-  // per-region survivors of the set's earlier chunks (a2 added them up)
-  if (threadIdx.x < 4) {
-    uint32_t b = 0;
-    const uint32_t* pt = reinterpret_cast<const uint32_t*>(w.ptot + sd.chunkP);
-    for (int q = 0; q < lc; q++) b += pt[4 * q + threadIdx.x];
-    carry[threadIdx.x] = b;
-  }
-  __syncthreads();
-  constexpr int per = kPlanTiles * kClsConsumers / kThreads;      // sub-slots per thread
-  const int64_t nslot = (int64_t)sd.ntile2 * kClsConsumers;
-  const int64_t s0 = (int64_t)lc * kPlanTiles * kClsConsumers + threadIdx.x * per;
-  const uint64_t* tc = w.tcnt + (size_t)sd.tile2 * kClsConsumers;
-  uint32_t own[4] = {0, 0, 0, 0};
-  for (int q = 0; q < per; q++) {
-    const int64_t t = s0 + q;
-    const uint64_t c = t < nslot ? tc[t] : 0ull;
+  if (w.ctl[s].status == 0 && lc < sd.nchunkP) {      // uniform across the CTA
+    if (warp == 0) {
+      // region totals of the set and of its chunks before this one
+      uint32_t t[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0};
+      const uint4* pt = w.ptot + sd.chunkP;
+      for (int k = lane; k < sd.nchunkP; k += 32) {
+        const uint4 v = pt[k];
+        t[0] += v.x; t[1] += v.y; t[2] += v.z; t[3] += v.w;
+        if (k < lc) { p[0] += v.x; p[1] += v.y; p[2] += v.z; p[3] += v.w; }
+      }
 #pragma unroll
-    for (int r = 0; r < 4; r++) own[r] += (uint32_t)(c >> (16 * r)) & 0xFFFFu;
-  }
-  uint32_t x[4];
-#pragma unroll
-  for (int r = 0; r < 4; r++) x[r] = own[r];
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[r], o);
-      if (lane >= o) x[r] += y;
+      for (int q = 0; q < 4; q++) {
+        t[q] = __reduce_add_sync(0xFFFFFFFFu, t[q]);
+        p[q] = __reduce_add_sync(0xFFFFFFFFu, p[q]);
+      }
+      if (lane == 0)
+        for (int q = 0; q < 4; q++) { sh_tot[q] = t[q]; sh_cpre[q] = p[q]; }
     }
-  }
-  if (lane == 31)
-    for (int r = 0; r < 4; r++) wsum[r][warp] = x[r];
-  __syncthreads();
-  uint32_t run[4];
+    const int64_t nsub = (int64_t)sd.ntile2 * kClsConsumers;
+    const int64_t g0 = (int64_t)lc * kPlanTiles * kClsConsumers + warp * kSubPerWarp;
+    const int64_t g1 = min(g0 + kSubPerWarp, nsub);
+    const uint64_t* tc = w.tcnt + (size_t)sd.tile2 * kClsConsumers;
+    uint32_t mt[4] = {0, 0, 0, 0};
+    for (int64_t g = g0 + lane; g < g1; g += 32) {
+      const uint64_t v = tc[g];
 #pragma unroll
-  for (int r = 0; r < 4; r++) {
-    run[r] = carry[r] + x[r] - own[r];
-    for (int q = 0; q < warp; q++) run[r] += wsum[r][q];
-  }
-  uint4* to = w.toff + (size_t)sd.tile2 * kClsConsumers;
-  for (int q = 0; q < per; q++) {
-    const int64_t t = s0 + q;
-    if (t >= nslot) break;
-    const uint64_t c = tc[t];
-    if (c) to[t] = make_uint4(run[0], run[1], run[2], run[3]);
-#pragma unroll
-    for (int r = 0; r < 4; r++) run[r] += (uint32_t)(c >> (16 * r)) & 0xFFFFu;
-  }
-  if (lc == sd.nchunkP - 1 && threadIdx.x == kThreads - 1) {
-    // the set's last chunk: run[] holds the set's totals
-    SetCtl& c = w.ctl[s];
-    uint32_t s1 = 0;
-    bool big = false;
-    for (int r = 0; r < 4; r++) {
-      c.cnt[r] = run[r];
-      s1 += run[r];
-      big |= run[r] > (uint32_t)kSmallMax;
+      for (int q = 0; q < 4; q++) mt[q] += (uint32_t)(v >> (16 * q)) & 0xFFFFu;
     }
-    c.s1 = s1;
-    if (big) c.flags |= SF_BIG;
+#pragma unroll
+    for (int q = 0; q < 4; q++) mt[q] = __reduce_add_sync(0xFFFFFFFFu, mt[q]);
+    if (lane == 0)
+      for (int q = 0; q < 4; q++) wtot[warp][q] = mt[q];
+    __syncthreads();
+    uint32_t pos[4], roff[4], acc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      pos[q] = sh_cpre[q];
+      for (int v = 0; v < warp; v++) pos[q] += wtot[v][q];
+      roff[q] = acc;
+      acc += sh_tot[q];
+    }
+    if (g0 < g1) move_subslots(j, w, sd, s, g0, g1, -1, pos, roff);
   }
-  // last CTA: plan the multi-CTA sort (big sets) and list the small segments
+  // last CTA: region totals of every set, the path of every set, the plans
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1017,76 +1010,35 @@ __global__ void __launch_bounds__(kThreads) k_plan(Job j, Ws w) {
   __syncthreads();
   if (!sh_last) return;
   __threadfence();
+  for (int s2 = warp; s2 < j.nsets; s2 += kWarps) {
+    const SetDesc d2 = get_set(j, s2);
+    SetCtl& c2 = w.ctl[s2];
+    if (c2.status != 0) continue;                     // uniform across the warp
+    uint32_t t[4] = {0, 0, 0, 0};
+    for (int k = lane; k < d2.nchunkP; k += 32) {
+      const uint4 v = w.ptot[d2.chunkP + k];
+      t[0] += v.x; t[1] += v.y; t[2] += v.z; t[3] += v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) t[q] = __reduce_add_sync(0xFFFFFFFFu, t[q]);
+    if (lane == 0) {
+      bool big = false;
+      for (int q = 0; q < 4; q++) { c2.cnt[q] = t[q]; big |= t[q] > (uint32_t)kSmallMax; }
+      c2.s1 = t[0] + t[1] + t[2] + t[3];
+      if (big) c2.flags |= SF_BIG;
+    }
+  }
+  __syncthreads();
   plan_sort(j, w);
   if (threadIdx.x == 0) {
     uint32_t k = 0;
     for (int s2 = 0; s2 < j.nsets; s2++) {
-      const SetCtl& c = w.ctl[s2];
-      if (c.status != 0 || (c.flags & SF_BIG)) continue;
+      const SetCtl& c2 = w.ctl[s2];
+      if (c2.status != 0 || (c2.flags & SF_BIG)) continue;
       for (int r = 0; r < 4; r++)
-        if (c.cnt[r]) w.small_seg[k++] = (uint32_t)(4 * s2 + r);
+        if (c2.cnt[r]) w.small_seg[k++] = (uint32_t)(4 * s2 + r);
     }
     w.ctr[CT_SMALL_TOTAL] = k;
-  }
-}
-
-// One warp per group of 32 sub-slots: stable move of each non-empty
-// sub-slot's survivors to their region-major positions in the set's stream.
-__global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  const int64_t nslots = (int64_t)j.ntile2 * kClsConsumers;
-  const int tile_pts = cls_tile(j.dtype), sub = tile_pts / kClsConsumers;
-  const int64_t nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t g0 = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * 32; g0 < nslots; g0 += nw * 32) {
-    const uint64_t mine = g0 + lane < nslots ? w.tcnt[g0 + lane] : 0ull;
-    uint32_t busy = __ballot_sync(0xFFFFFFFFu, mine != 0);
-    while (busy) {
-      const int l = __ffs(busy) - 1;
-      busy &= busy - 1;
-      const int64_t slot = g0 + l;
-      const uint64_t tc = __shfl_sync(0xFFFFFFFFu, mine, l);
-      const int tile = (int)(slot / kClsConsumers), cw = (int)(slot % kClsConsumers);
-      int s = 0;
-      if (j.sets) {
-        int lo = 0, hi = j.nsets - 1;
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (j.sets[mid].tile2 <= tile) lo = mid; else hi = mid - 1;
-        }
-        s = lo;
-      }
-      const SetDesc sd = get_set(j, s);
-      const SetCtl& c = w.ctl[s];
-      const uint4 of = w.toff[slot];
-      uint32_t base[4];
-      base[0] = of.x;
-      base[1] = c.cnt[0] + of.y;
-      base[2] = c.cnt[0] + c.cnt[1] + of.z;
-      base[3] = c.cnt[0] + c.cnt[1] + c.cnt[2] + of.w;
-      const uint32_t n = (uint32_t)(tc & 0xFFFFu) + (uint32_t)((tc >> 16) & 0xFFFFu) +
-                         (uint32_t)((tc >> 32) & 0xFFFFu) + (uint32_t)(tc >> 48);
-      const int64_t src = sd.off + (int64_t)(tile - sd.tile2) * tile_pts + (int64_t)cw * sub;
-      for (uint32_t i0 = 0; i0 < n; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        const bool ok = i < n;
-        const uint64_t key = ok ? w.keyB[src + i] : 0;
-        const uint32_t val = ok ? w.valB[src + i] : 0;
-        const uint64_t spv = ok ? w.spvB[src + i] : 0;
-        const int r = ok ? (int)(val >> 30) : -1;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const uint32_t b = __ballot_sync(0xFFFFFFFFu, r == q);
-          if (r == q) {
-            const uint32_t pos = base[q] + __popc(b & lt_mask);
-            w.keyA[sd.off + pos] = key;
-            w.valA[sd.off + pos] = val;
-            w.spvA[sd.off + pos] = spv;
-          }
-          base[q] += __popc(b);
-        }
-      }
-    }
   }
 }
 
@@ -1112,12 +1064,8 @@ int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
 }
 
 int launch_gather(const Job& j, const Ws& w, const Launch& L) {
-  k_plan<<<j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream>>>(j, w);
-  int gg = (int)(((int64_t)j.ntile2 * kClsConsumers + 32 * kWarps - 1) / (32 * kWarps));
-  if (gg > L.grid_cap) gg = L.grid_cap;
-  if (gg < 1) gg = 1;
-  k_gather<<<gg, kThreads, 0, L.stream>>>(j, w);
-  return 2;
+  k_gather<<<j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream>>>(j, w);
+  return 1;
 }
 
 int launch_classify(const Job& j, const Ws& w, const Launch& L) {

@@ -71,7 +71,6 @@ size_t na_layout(int64_t n, int32_t nchunk1, int32_t ntile2, char* base, Ws& w, 
   status_bytes = o - status_off;
   w.part = (Part*)take(sizeof(Part) * (size_t)(nchunk1 > 0 ? nchunk1 : 1));
   w.tcnt = (uint64_t*)take(8 * 8 * (size_t)(ntile2 > 0 ? ntile2 : 1));
-  w.toff = (uint4*)take(16 * 8 * (size_t)(ntile2 > 0 ? ntile2 : 1));
   w.small_seg = (uint32_t*)take(16);
   w.keyA = (uint64_t*)take(8 * (size_t)n);
   w.keyB = (uint64_t*)take(8 * (size_t)n);
