@@ -382,21 +382,87 @@ __device__ __forceinline__ int orient_f32_filter(float2 A, float2 B, float2 C) {
   return 0;
 }
 
-// Exact orientation of float64 points, FP32-filtered first when `filt` (the
-// set's coordinates are below 2^60 and A, B, C are their f64_trunc_f32 views).
-__device__ __forceinline__ int orient_f64_views(double2 a, double2 b, double2 c, float2 A, float2 B,
-                                                float2 C, bool filt) {
+// Split of a float64 coordinate into two floats, x = h + l + d: h is the
+// f64_trunc_f32 view (x with its 29 low significand bits cleared), l the
+// float nearest to the cleared part x - h (an integer of 29 bits scaled by
+// 2^(e - 1075), converted exactly up to one rounding), so |d| <= 2^-24 |x - h|
+// <= 2^-47 |x|.  Defined for x = 0 and 2^-60 <= |x| <= 2^60; otherwise h is a
+// NaN, which leaves every filter below undecided.
+__device__ __forceinline__ float2 f64_split(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  if ((b << 1) == 0) return make_float2(0.f, 0.f);
+  const uint32_t hw = (uint32_t)(b >> 32);
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  if (e < 1023 - 60 || e > 1023 + 60) return make_float2(__int_as_float(0x7FC00000), 0.f);
+  const float scale = __uint_as_float((uint32_t)(e - 1075 + 127) << 23);   // 2^(e-1075), normal
+  const float lo = __fmul_rn(__uint2float_rn((uint32_t)b & 0x1FFFFFFFu), scale);
+  return make_float2(f64_trunc_f32(b), (hw & 0x80000000u) ? -lo : lo);
+}
+
+// Second FP32 filter of orient(a,b,c), on split points (h.x, h.y, l.x, l.y)
+// from f64_split.  A difference of two coordinates is taken as
+// D = fl(fl(Ph - Ah) + fl(Pl - Al)); with mu = 2^-24, eta = 2^-149 and M the
+// largest |h| of the three points, it is within
+//   e = mu (|Ph - Ah| + |Pl - Al| + |D|) + 2^-46 (1 + 2^-22) M + 3 eta
+// of the exact difference (each rounding is within mu of its result or eta
+// absolute; the split errors add at most 2^-47 (|P| + |A|)).  With the four
+// differences U1, V1, U2, V2 and their bounds e1..e4, det = fma(U1, V2,
+// -fl(V1 U2)) is within
+//   E = e1 |V2| + e4 |U1| + e1 e4 + e2 |U2| + e3 |V1| + e2 e3
+//       + mu |V1 U2| + mu |det| + 2 eta
+// of the exact determinant.  Returns its sign when |det| (1 - 2 mu) exceeds
+// 1.01 E + 2^-146 (covering the rounding and underflow of evaluating E), else
+// 0.  Unlike orient_f32_filter, whose error grows with the coordinates'
+// magnitude, this one is relative to the differences, so it decides the
+// nearly collinear triples of closely spaced points.
+__device__ __forceinline__ int orient_split_filter(float4 A, float4 B, float4 C) {
+  const float mu = 5.9604645e-08f;
+  const float M = fmaxf(fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(B.x), fabsf(B.y))),
+                        fmaxf(fabsf(C.x), fabsf(C.y)));
+  const float c0 = __fmaf_ru(1.4210859e-14f, M, 4.3e-45f);          // 2^-46 (1 + 2^-22) M + 3 eta
+  float e1, e2, e3, e4;
+  const float U1 = __fadd_rn(__fsub_rn(B.x, A.x), __fsub_rn(B.z, A.z));
+  e1 = __fmaf_ru(mu, __fadd_ru(__fadd_ru(fabsf(__fsub_rn(B.x, A.x)), fabsf(__fsub_rn(B.z, A.z))), fabsf(U1)), c0);
+  const float V1 = __fadd_rn(__fsub_rn(B.y, A.y), __fsub_rn(B.w, A.w));
+  e2 = __fmaf_ru(mu, __fadd_ru(__fadd_ru(fabsf(__fsub_rn(B.y, A.y)), fabsf(__fsub_rn(B.w, A.w))), fabsf(V1)), c0);
+  const float U2 = __fadd_rn(__fsub_rn(C.x, A.x), __fsub_rn(C.z, A.z));
+  e3 = __fmaf_ru(mu, __fadd_ru(__fadd_ru(fabsf(__fsub_rn(C.x, A.x)), fabsf(__fsub_rn(C.z, A.z))), fabsf(U2)), c0);
+  const float V2 = __fadd_rn(__fsub_rn(C.y, A.y), __fsub_rn(C.w, A.w));
+  e4 = __fmaf_ru(mu, __fadd_ru(__fadd_ru(fabsf(__fsub_rn(C.y, A.y)), fabsf(__fsub_rn(C.w, A.w))), fabsf(V2)), c0);
+  const float p = __fmul_rn(V1, U2);
+  const float det = __fmaf_rn(U1, V2, -p);
+  float E = __fmul_ru(e1, fabsf(V2));
+  E = __fmaf_ru(e4, fabsf(U1), E);
+  E = __fmaf_ru(e1, e4, E);
+  E = __fmaf_ru(e2, fabsf(U2), E);
+  E = __fmaf_ru(e3, fabsf(V1), E);
+  E = __fmaf_ru(e2, e3, E);
+  E = __fmaf_ru(mu, __fadd_ru(fabsf(p), fabsf(det)), E);
+  E = __fmaf_ru(1.01f, E, 1.5e-44f);                                // + 2 eta + 2^-146 slack
+  if (__fmul_rd(fabsf(det), 0.99999988f) > E) return det > 0.f ? 1 : -1;
+  return 0;
+}
+
+// Split point (h.x, h.y, l.x, l.y) of f64_split.
+__device__ __forceinline__ float4 f64_split4(double2 p) {
+  const float2 x = f64_split(p.x), y = f64_split(p.y);
+  return make_float4(x.x, y.x, x.y, y.y);
+}
+
+// Exact orientation of float64 points from their split forms: the view
+// filter, then the split filter (when `filt`: coordinates below 2^60), then
+// the FP64 filter and expansion arithmetic.
+__device__ __forceinline__ int orient_f64_split(double2 a, double2 b, double2 c, float4 A, float4 B,
+                                                float4 C, bool filt) {
   if (filt) {
-    const int o = orient_f32_filter(A, B, C);
+    int o = orient_f32_filter(make_float2(A.x, A.y), make_float2(B.x, B.y), make_float2(C.x, C.y));
+    if (o) return o;
+    o = orient_split_filter(A, B, C);
     if (o) return o;
   }
   return orient_f64(a.x, a.y, b.x, b.y, c.x, c.y);
 }
 
-__device__ __forceinline__ float2 f64_view2(double2 p) {
-  return make_float2(f64_trunc_f32((uint64_t)__double_as_longlong(p.x)),
-                     f64_trunc_f32((uint64_t)__double_as_longlong(p.y)));
-}
 
 // ------------------------------------------------- memory-order helpers
 __device__ __forceinline__ uint64_t ld_acq_u64(const uint64_t* p) {

@@ -65,16 +65,16 @@ __device__ void merge_chains(A& acc, int& hl, int& tl, int hr, int tr) {
 // exactly in 64/128-bit integers.
 template <int DT>
 __device__ __forceinline__ int orient_chain(const typename PT<DT>::T& a, const typename PT<DT>::T& b,
-                                            const typename PT<DT>::T& c, float2 A, float2 B, float2 C,
+                                            const typename PT<DT>::T& c, float4 A, float4 B, float4 C,
                                             bool flag) {
-  if constexpr (DT == DT_F64) return orient_f64_views(a, b, c, A, B, C, flag);
+  if constexpr (DT == DT_F64) return orient_f64_split(a, b, c, A, B, C, flag);
   else return orient_i32(a.x, a.y, b.x, b.y, c.x, c.y, flag);
 }
 
 template <int DT>
 struct SmemAcc {
   typename PT<DT>::T* p;
-  float2* f;          // FP32 views (float64 only)
+  float4* f;          // FP32 split points (float64 only)
   uint16_t* pv;
   uint16_t* nx;
   uint8_t* al;
@@ -85,7 +85,7 @@ struct SmemAcc {
   __device__ __forceinline__ void link(int a, int b) { nx[a] = (uint16_t)b; pv[b] = (uint16_t)a; }
   __device__ __forceinline__ int orient(int i, int j, int k) const {
     if constexpr (DT == DT_F64) return orient_chain<DT>(p[i], p[j], p[k], f[i], f[j], f[k], flag);
-    else return orient_chain<DT>(p[i], p[j], p[k], float2{}, float2{}, float2{}, flag);
+    else return orient_chain<DT>(p[i], p[j], p[k], float4{}, float4{}, float4{}, flag);
   }
 };
 
@@ -102,14 +102,54 @@ struct GlobAcc {
   __device__ __forceinline__ void link(int a, int b) { nx[a] = (uint32_t)b; pv[b] = (uint32_t)a; }
   __device__ __forceinline__ int orient(int i, int j, int k) const {
     const typename PT<DT>::T a = p[i], b = p[j], c = p[k];
-    if constexpr (DT == DT_F64) return orient_chain<DT>(a, b, c, f64_view2(a), f64_view2(b), f64_view2(c), flag);
-    else return orient_chain<DT>(a, b, c, float2{}, float2{}, float2{}, flag);
+    if constexpr (DT == DT_F64) return orient_chain<DT>(a, b, c, f64_split4(a), f64_split4(b), f64_split4(c), flag);
+    else return orient_chain<DT>(a, b, c, float4{}, float4{}, float4{}, flag);
   }
 };
 
+constexpr int kPeelRounds = 48;   // peeling rounds before the stack-and-merge fallback
+
+// Exclusive prefix sum of one value per thread over the CTA; sh[kWarps]
+// receives the total.  Ends with the CTA synchronised.
+__device__ __forceinline__ int block_excl_sum(int v, int* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  int pre = x - v, tot = 0;
+  for (int q = 0; q < kWarps; q++) {
+    if (q < warp) pre += sh[q];
+    tot += sh[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh[kWarps] = tot;
+  __syncthreads();
+  return pre;
+}
+
+// Positions i < m with al[i] != 0, in order, into out; returns their count.
+__device__ __forceinline__ int block_compact(const uint8_t* al, int m, uint16_t* out, int* sh) {
+  const int per = (m + kThreads - 1) / kThreads;
+  const int i0 = threadIdx.x * per;
+  int c = 0;
+  for (int q = 0; q < per; q++) c += (i0 + q < m && al[i0 + q]) ? 1 : 0;
+  int pre = block_excl_sum(c, sh);
+  for (int q = 0; q < per; q++)
+    if (i0 + q < m && al[i0 + q]) out[pre++] = (uint16_t)(i0 + q);
+  const int n = sh[kWarps];
+  __syncthreads();
+  return n;
+}
+
 template <int DT>
 constexpr size_t chain_local_smem() {
-  return (size_t)kChainBlk * (sizeof(typename PT<DT>::T) + (DT == DT_F64 ? 8 : 0) + 2 + 2 + 2 + 1) +
+  return (size_t)kChainBlk * (sizeof(typename PT<DT>::T) + (DT == DT_F64 ? 16 : 0) + 2 + 2 + 2 + 1) +
          2 * kThreads * sizeof(int);
 }
 
@@ -118,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
   using P = typename PT<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   P* sp = reinterpret_cast<P*>(smem);
-  float2* sf = reinterpret_cast<float2*>(sp + kChainBlk);              // views (float64 only)
+  float4* sf = reinterpret_cast<float4*>(sp + kChainBlk);              // split points (float64 only)
   uint16_t* pv = reinterpret_cast<uint16_t*>(DT == DT_F64 ? (void*)(sf + kChainBlk) : (void*)(sp + kChainBlk));
   uint16_t* nx = pv + kChainBlk;
   uint16_t* stk = nx + kChainBlk;
@@ -126,6 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
   int* gt = gh + kThreads;
   uint8_t* al = reinterpret_cast<uint8_t*>(gt + kThreads);
   __shared__ P pred;
+  __shared__ int sh_cnt[kWarps + 1];
 
   const uint32_t total = w.ctr[CT_CHAIN_TOTAL];
   P* cp = reinterpret_cast<P*>(w.cpts);
@@ -153,43 +194,102 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
         v = cp[cb + p];
       }
       sp[i] = v;
-      if constexpr (DT == DT_F64) sf[i] = f64_view2(v);
+      if constexpr (DT == DT_F64) sf[i] = f64_split4(v);
     }
     if (threadIdx.x == 0 && p0 > 0) pred = cp[cb + p0 - 1];
     __syncthreads();
 
     SmemAcc<DT> acc{sp, sf, pv, nx, al, flag};
-    // per thread: strict left-turn stack over its 16 positions
-    const int i0 = threadIdx.x * kChainItems;
-    const int i1 = min(m, i0 + kChainItems);
-    int top = 0;
-    for (int i = i0; i < i1; i++) {
+    // identical neighbours: the first index stays
+    for (int i = threadIdx.x; i < m; i += kThreads) {
       bool dup;
       if (i > 0) dup = same_pt<DT>(sp[i], sp[i - 1]);
       else dup = p0 > 0 && same_pt<DT>(sp[0], pred);
-      if (dup) { al[i] = 0; continue; }
-      while (top >= 2 && acc.orient(stk[i0 + top - 2], stk[i0 + top - 1], i) <= 0) {
-        al[stk[i0 + top - 1]] = 0;
-        top--;
+      al[i] = dup ? 0 : 1;
+    }
+    __syncthreads();
+    // Peeling: every inner point of the block's current sequence that does
+    // not make a strict left turn with its two current neighbours is no
+    // strict vertex of the chain's hull (it lies on or inside the segment
+    // between two chain points around it), so all of them go at once.  When
+    // a round removes nothing the sequence is locally convex everywhere,
+    // i.e. it is the block's convex chain.  The block's first and last points
+    // stay (their neighbours lie in other blocks).
+    uint16_t* cur = stk;
+    uint16_t* nxt = nx;
+    int n = block_compact(al, m, cur, sh_cnt);
+    bool conv = false;
+    for (int round = 0; round < kPeelRounds && !conv; round++) {
+      const int per = (n + kThreads - 1) / kThreads;
+      const int t0 = threadIdx.x * per;
+      uint32_t keep = 0;
+      for (int q = 0; q < per; q++) {
+        const int t = t0 + q;
+        if (t >= n) break;
+        bool k = true;
+        if (t > 0 && t < n - 1) k = acc.orient(cur[t - 1], cur[t], cur[t + 1]) > 0;
+        keep |= (uint32_t)k << q;
       }
-      stk[i0 + top++] = (uint16_t)i;
-      al[i] = 1;
-    }
-    for (int q = 0; q + 1 < top; q++) {
-      nx[stk[i0 + q]] = stk[i0 + q + 1];
-      pv[stk[i0 + q + 1]] = stk[i0 + q];
-    }
-    gh[threadIdx.x] = top ? stk[i0] : -1;
-    gt[threadIdx.x] = top ? stk[i0 + top - 1] : -1;
-
-    for (int step = 1; step < kThreads; step <<= 1) {
+      const int nk = __popc(keep);
+      int pre = block_excl_sum(nk, sh_cnt);
+      const int n2 = sh_cnt[kWarps];
+      for (int q = 0; q < per; q++) {
+        const int t = t0 + q;
+        if (t >= n) break;
+        if ((keep >> q) & 1u) nxt[pre++] = cur[t];
+        else al[cur[t]] = 0;
+      }
       __syncthreads();
-      const int t = threadIdx.x;
-      if ((t & (2 * step - 1)) == 0 && t + step < kThreads && (t + step) * kChainItems < m) {
-        int hl = gh[t], tl = gt[t];
-        merge_chains(acc, hl, tl, gh[t + step], gt[t + step]);
-        gh[t] = hl;
-        gt[t] = tl;
+      conv = n2 == n;
+      n = n2;
+      uint16_t* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (conv) {
+      // links of the convex sequence (held in stk, so that nx is free)
+      if (cur != stk) {
+        for (int t = threadIdx.x; t < n; t += kThreads) stk[t] = cur[t];
+        __syncthreads();
+        cur = stk;
+      }
+      for (int t = threadIdx.x; t < n; t += kThreads) {
+        const int i = cur[t];
+        if (t > 0) pv[i] = cur[t - 1];
+        if (t + 1 < n) nx[i] = cur[t + 1];
+      }
+      if (threadIdx.x == 0) {
+        gh[0] = n ? cur[0] : -1;
+        gt[0] = n ? cur[n - 1] : -1;
+      }
+    } else {
+      // not converged: per thread a strict left-turn stack over its 16
+      // positions (peeled points skipped), then pairwise merges
+      __syncthreads();
+      const int i0 = threadIdx.x * kChainItems;
+      const int i1 = min(m, i0 + kChainItems);
+      int top = 0;
+      for (int i = i0; i < i1; i++) {
+        if (!al[i]) continue;
+        while (top >= 2 && acc.orient(stk[i0 + top - 2], stk[i0 + top - 1], i) <= 0) {
+          al[stk[i0 + top - 1]] = 0;
+          top--;
+        }
+        stk[i0 + top++] = (uint16_t)i;
+      }
+      for (int q = 0; q + 1 < top; q++) {
+        nx[stk[i0 + q]] = stk[i0 + q + 1];
+        pv[stk[i0 + q + 1]] = stk[i0 + q];
+      }
+      gh[threadIdx.x] = top ? stk[i0] : -1;
+      gt[threadIdx.x] = top ? stk[i0 + top - 1] : -1;
+      for (int step = 1; step < kThreads; step <<= 1) {
+        __syncthreads();
+        const int t = threadIdx.x;
+        if ((t & (2 * step - 1)) == 0 && t + step < kThreads && (t + step) * kChainItems < m) {
+          int hl = gh[t], tl = gt[t];
+          merge_chains(acc, hl, tl, gh[t + step], gt[t + step]);
+          gh[t] = hl;
+          gt[t] = tl;
+        }
       }
     }
     __syncthreads();

@@ -105,6 +105,24 @@ def test_shell_and_far_from_origin():
     check(inputs.disk_f64(100_000, 5) * 2.0 ** -300)
 
 
+def test_nearly_collinear_chains():
+    """Closely spaced hull points: orientation determinants far below the
+    coordinates' FP32 resolution (the split filter and the exact fallback)."""
+    rng = np.random.default_rng(41)
+    # tiny circle away from the origin: every point is a hull vertex
+    t = 2.0 * np.pi * rng.permutation(60_000) / 60_000
+    check(np.stack([0.3 + 1e-6 * np.cos(t), -0.7 + 1e-6 * np.sin(t)], 1))
+    # dense unit circle: neighbours 3e-6 apart
+    check(inputs.circle_f64(2_000_003, seed=8))
+    # a line with noise at the last bits, and a parabola on a fine grid
+    x = rng.random(200_000)
+    check(np.stack([x, 0.5 * x + 0.25 + 1e-15 * rng.standard_normal(200_000)], 1))
+    g = np.arange(-50_000, 50_001) / 50_000.0
+    g = g[rng.permutation(len(g))]
+    check(np.stack([g, g * g], 1))
+    check(np.stack([1e5 + g, 3e5 - g * g], 1))
+
+
 # ------------------------------------------------------------ stages
 
 STAGE_KINDS = {
