@@ -138,9 +138,13 @@ int cch_hull_stages(const void *points, int64_t n, int dtype, uint32_t opts,
  * cch_profile_read synchronises on the recorded events, writes the summed
  * milliseconds per stage to stage_ms[0 .. min(7, max_stages)), the number of
  * calls to *calls (if not NULL), forgets them, and returns the number of
- * stages (7).  cch_profile(0) stops recording.
+ * stages (7).  cch_profile(0) stops recording.  cch_profile_stages(mask)
+ * records only around the stages whose bit is set in mask (bit k: stage k;
+ * the others read as 0), which keeps the events' own cost out of the rest
+ * of the pipeline; mask 0 stops recording.
  */
 int cch_profile(int enable);
+int cch_profile_stages(uint32_t mask);
 int cch_profile_read(double *stage_ms, int max_stages, int64_t *calls);
 
 /* Number of CUDA kernels this library has launched since it was loaded. */

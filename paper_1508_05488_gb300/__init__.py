@@ -63,6 +63,8 @@ def _load():
         lib.cch_release_workspace.argtypes = []
         lib.cch_profile.restype = ctypes.c_int
         lib.cch_profile.argtypes = [ctypes.c_int]
+        lib.cch_profile_stages.restype = ctypes.c_int
+        lib.cch_profile_stages.argtypes = [ctypes.c_uint32]
         lib.cch_profile_read.restype = ctypes.c_int
         lib.cch_profile_read.argtypes = [vp, ctypes.c_int, vp]
         lib.cch_launch_count.restype = ctypes.c_uint64
@@ -251,6 +253,14 @@ STAGE_NAMES = ("k_extremes", "k_stairs", "k_classify", "gather", "small", "big",
 def profile(enable: bool = True):
     """Record CUDA events around the pipeline stages of every later call."""
     _check(_load().cch_profile(1 if enable else 0), "cch_profile")
+
+
+def profile_stages(names) -> None:
+    """Record events only around the named stages (see STAGE_NAMES)."""
+    mask = 0
+    for n in names:
+        mask |= 1 << STAGE_NAMES.index(n)
+    _check(_load().cch_profile_stages(mask), "cch_profile_stages")
 
 
 def profile_read() -> tuple[dict, int]:

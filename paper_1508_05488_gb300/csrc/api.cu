@@ -112,14 +112,15 @@ std::atomic<uint64_t> g_launches{0};
 // Optional stage timing: CUDA events around the stages of every call, read
 // back (and summed) by cch_profile_read.
 constexpr int kStages = 7;   // a1, stairs, a2, gather, small path, multi-block path, chain
-struct ProfRec { cudaEvent_t ev[kStages + 1]; };
-bool g_prof = false;
+struct ProfRec { cudaEvent_t ev[kStages + 1]; uint32_t mask; };
+uint32_t g_prof = 0;   // stages whose boundaries get events (bit k: stage k)
 std::vector<ProfRec> g_prof_pending, g_prof_free;
 
 cudaEvent_t* prof_begin(ProfRec& rec) {
   if (!g_prof) return nullptr;
   if (!g_prof_free.empty()) { rec = g_prof_free.back(); g_prof_free.pop_back(); }
   else for (auto& e : rec.ev) cudaEventCreate(&e);
+  rec.mask = g_prof;
   return rec.ev;
 }
 int g_sms = 0;
@@ -221,22 +222,27 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
   ProfRec rec{};
   cudaEvent_t* ev = prof_begin(rec);
   int nk = 0;
-  if (ev) cudaEventRecord(ev[0], stream);
+  // event k marks the start of stage k (and the end of stage k - 1)
+  auto mark = [&](int k) {
+    if (ev && ((rec.mask >> k) & 1u || (k > 0 && (rec.mask >> (k - 1)) & 1u))) cudaEventRecord(ev[k], stream);
+  };
+  mark(0);
   nk += launch_extremes(j, L.w, La);
-  if (ev) cudaEventRecord(ev[1], stream);
+  mark(1);
   nk += launch_stairs(j, L.w, La);
-  if (ev) cudaEventRecord(ev[2], stream);
+  mark(2);
   nk += launch_classify(j, L.w, La);
-  if (ev) cudaEventRecord(ev[3], stream);
+  mark(3);
   nk += launch_gather(j, L.w, La);
-  if (ev) cudaEventRecord(ev[4], stream);
+  mark(4);
   nk += launch_small(j, L.w, La);
-  if (ev) cudaEventRecord(ev[5], stream);
+  mark(5);
   nk += launch_big(j, L.w, La);
-  if (ev) cudaEventRecord(ev[6], stream);
+  mark(6);
   nk += launch_chain(j, L.w, La);
   if (stages) { launch_extract_spa(j, L.w, stages->spa_idx, stream); nk++; }
-  if (ev) { cudaEventRecord(ev[7], stream); g_prof_pending.push_back(rec); }
+  mark(7);
+  if (ev) g_prof_pending.push_back(rec);
   g_launches += (uint64_t)nk;
   if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
   if (ws_out) *ws_out = ws;
@@ -430,7 +436,13 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
 
 int cch_profile(int enable) {
   std::lock_guard<std::mutex> lk(g_mu);
-  g_prof = enable != 0;
+  g_prof = enable != 0 ? (1u << kStages) - 1u : 0u;
+  return CCH_OK;
+}
+
+int cch_profile_stages(uint32_t mask) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_prof = mask & ((1u << kStages) - 1u);
   return CCH_OK;
 }
 
@@ -440,8 +452,12 @@ int cch_profile_read(double* stage_ms, int max_stages, int64_t* calls) {
   for (int k = 0; k < max_stages; k++) stage_ms[k] = 0.0;
   int64_t n = 0;
   for (auto& rec : g_prof_pending) {
-    if (cudaEventSynchronize(rec.ev[kStages]) != cudaSuccess) return CCH_ERR_CUDA;
+    int last = 0;
+    for (int k = 0; k < kStages; k++)
+      if ((rec.mask >> k) & 1u) last = k + 1;
+    if (cudaEventSynchronize(rec.ev[last]) != cudaSuccess) return CCH_ERR_CUDA;
     for (int k = 0; k < kStages && k < max_stages; k++) {
+      if (!((rec.mask >> k) & 1u)) continue;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, rec.ev[k], rec.ev[k + 1]);
       stage_ms[k] += ms;
