@@ -311,11 +311,33 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
   c.flags = flags;
 }
 
+constexpr int kExtStages = 3;                          // TMA ring depth of a1
+constexpr int kExtBlock = (kClsConsumers + 1) * 32;    // 8 consumer warps + a producer warp
+constexpr int kExtSmem = kExtStages * (kClsTileBytes + 16);
+
+// Barrier of the consumer warps only (the producer warp has left).
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" :: "r"(kClsConsumers * 32) : "memory");
+}
+
+// a1.  nchunk1 CTAs per set; CTA k takes the set's tiles k, k + nchunk1,
+// k + 2 nchunk1, ... (all CTAs read close together in memory).  Warp 8
+// streams them through a ring of shared-memory stages with 1-D TMA bulk
+// copies (full/empty mbarriers); warps 0..7 each scan a contiguous eighth of
+// every tile, so every thread meets its points in increasing index order.
 template <int DT>
-__global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
+__global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   using P = typename PointT<DT>::T;
-  __shared__ Lex red[kWarps][4];
-  __shared__ uint32_t red_amin[kWarps];
+  constexpr int PB = (int)sizeof(P);
+  constexpr int TILE = kClsTileBytes / PB;
+  constexpr int WPTS = TILE / kClsConsumers;
+  constexpr int IW = WPTS / 32;
+  constexpr int SB = kClsTileBytes + 16;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kExtStages], empty[kExtStages];
+  __shared__ int st_head[kExtStages];
+  __shared__ Lex red[kClsConsumers][4];
+  __shared__ uint32_t red_amin[kClsConsumers];
   __shared__ int last;
 
   const int chunk = blockIdx.x;
@@ -329,65 +351,121 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
     s = lo;
   }
   const SetDesc sd = get_set(j, s);
-  const int64_t c0 = (int64_t)(chunk - sd.chunk1) * j.chunk1_len;
-  const int64_t c1 = min(sd.n, c0 + j.chunk1_len);
-  const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
+  const int64_t tiles_set = (sd.n + TILE - 1) / TILE;
+  const int64_t k0 = chunk - sd.chunk1, kstep = sd.nchunk1;
+  const int ntile = k0 < tiles_set ? (int)((tiles_set - k0 + kstep - 1) / kstep) : 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int q = 0; q < kExtStages; q++) { mbar_init(&full[q], 1); mbar_init(&empty[q], kClsConsumers); }
+    fence_mbar_init();
+    fence_async_smem();
+  }
+  __syncthreads();
 
+  if (warp == kClsConsumers) {
+    // ---------------------------------------------------------- producer
+    if (lane != 0) return;
+    int issued = 0;
+    bool ok = true;
+    for (int it = 0; it < ntile; it++) {
+      const int slot = it % kExtStages;
+      if (it >= kExtStages) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&empty[slot], (uint32_t)((it / kExtStages) - 1) & 1u))
+          if (!spin_step(spins, w.ctr)) { ok = false; break; }
+        if (!ok) break;
+        fence_async_smem();
+      }
+      const int64_t i0 = (k0 + (int64_t)it * kstep) * TILE;
+      const int np = (int)min((int64_t)TILE, sd.n - i0);
+      const char* src = reinterpret_cast<const char*>(j.pts) + (sd.off + i0) * PB;
+      unsigned char* dst = smem + slot * SB + 16;
+      const int head = ((uintptr_t)src & 15) ? 1 : 0;       // int32 only
+      const int rem = np - head;
+      const int tail = ((rem * PB) & 15) ? 1 : 0;
+      const uint32_t bytes = (uint32_t)(rem - tail) * PB;
+      st_head[slot] = head;
+      if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
+      if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
+      mbar_arrive_tx(&full[slot], bytes);
+      if (bytes) tma_load_1d(dst, src + head * PB, bytes, &full[slot]);
+      issued = it + 1;
+    }
+    if (!ok) {
+      // a wait ran out: let the copies already issued land before exiting
+      for (int it = max(0, issued - kExtStages); it < issued; it++) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&full[it % kExtStages], (uint32_t)(it / kExtStages) & 1u))
+          if (!spin_step(spins, w.ctr) && spins > kSpinLimit) break;
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
   Lex best[4];
   uint32_t th[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; th[k] = 0xFFFFFFFFu; }
   uint32_t amin = 0x7FFFFFFFu;
-
   // set-local indices fit in 32 bits (n <= 2^30)
-  constexpr int U = 4;
-  const uint32_t e0 = (uint32_t)c0, e1 = (uint32_t)c1;
-  for (uint32_t base = e0; base < e1; base += kThreads * U) {
-    P v[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const uint32_t i = base + u * kThreads + threadIdx.x;
-      if (i < e1) v[u] = __ldcs(pts + i);
+  for (int it = 0; it < ntile; it++) {
+    const int slot = it % kExtStages;
+    {
+      uint32_t spins = 0;
+      bool ok = true;
+      while (!mbar_try_wait(&full[slot], (uint32_t)(it / kExtStages) & 1u))
+        if (!spin_step(spins, w.ctr)) { ok = false; break; }
+      if (!ok) break;
     }
-    uint32_t xh[U], xl[U], yh[U], yl[U];
+    const int64_t t0 = (k0 + (int64_t)it * kstep) * TILE;
+    const uint32_t i0 = (uint32_t)t0;
+    const int np = (int)min((int64_t)TILE, sd.n - t0);
+    const unsigned char* base = smem + slot * SB + 16 - st_head[slot] * PB;
+    const int wb = warp * WPTS;
+    uint32_t xh[IW], xl[IW], yh[IW], yl[IW];
     bool need = false;
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const uint32_t i = base + u * kThreads + threadIdx.x;
-      if (i < e1) {
-        a1_words<DT>(v[u], xh[u], xl[u], yh[u], yl[u], amin);
-        need |= a1_maybe(xh[u], yh[u], th);
+    for (int k = 0; k < IW; k++) {
+      const int i = wb + k * 32 + lane;
+      if (i < np) {
+        const P p = *reinterpret_cast<const P*>(base + i * PB);
+        a1_words<DT>(p, xh[k], xl[k], yh[k], yl[k], amin);
+        need |= a1_maybe(xh[k], yh[k], th);
       } else {
-        xh[u] = yh[u] = 0xFFFFFFFFu;   // never read: need stays per point below
+        xh[k] = yh[k] = 0xFFFFFFFFu;
+        xl[k] = yl[k] = 0u;
       }
     }
+    __syncwarp();
+    if (lane == 0)   // the warp is done with the stage: release it to the producer
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
     // rare: a warp-uniform branch keeps the full update out of the hot path
     if (__any_sync(0xFFFFFFFFu, need)) {
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const uint32_t i = base + u * kThreads + threadIdx.x;
-        if (i < e1 && a1_maybe(xh[u], yh[u], th)) a1_update<DT>(xh[u], xl[u], yh[u], yl[u], i, best);
+      for (int k = 0; k < IW; k++) {
+        const int i = wb + k * 32 + lane;
+        if (i < np && a1_maybe(xh[k], yh[k], th)) a1_update<DT>(xh[k], xl[k], yh[k], yl[k], i0 + i, best);
       }
       a1_thresholds(best, th);
     }
   }
 
-  // CTA reduction
+  // reduction over the consumer warps
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
     amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
     red_amin[warp] = amin;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < kWarps; q++) {
+  consumers_sync();
+  if (tid == 0) {
+    for (int q = 1; q < kClsConsumers; q++) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
       amin = min(amin, red_amin[q]);
     }
@@ -397,20 +475,20 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
     __threadfence();
     last = atomicAdd(&w.ctl[s].arrive1, 1u) == (uint32_t)(sd.nchunk1 - 1);
   }
-  __syncthreads();
+  consumers_sync();
   if (!last) return;
 
   // Last chunk of the set: reduce the set's partials, clear its sort
   // histogram and stairs table, set up its edges.
   __threadfence();
   uint32_t* hist = w.hist + (size_t)s * kSortPasses * 256;
-  for (int i = threadIdx.x; i < kSortPasses * 256; i += kThreads) hist[i] = 0;
+  for (int i = threadIdx.x; i < kSortPasses * 256; i += kClsConsumers * 32) hist[i] = 0;
   uint32_t* stt = w.stairs + (size_t)s * 4 * kStairB;
-  for (int i = threadIdx.x; i < 4 * kStairB; i += kThreads) stt[i] = 0xFFFFFFFFu;
+  for (int i = threadIdx.x; i < 4 * kStairB; i += kClsConsumers * 32) stt[i] = 0xFFFFFFFFu;
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
   amin = 0x7FFFFFFFu;
-  for (int q = threadIdx.x; q < sd.nchunk1; q += kThreads) {
+  for (int q = threadIdx.x; q < sd.nchunk1; q += kClsConsumers * 32) {
     const Part& pt = w.part[sd.chunk1 + q];
     for (int k = 0; k < 4; k++) {
       Lex v{pt.k1[k], pt.k2[k], pt.idx[k]};
@@ -424,15 +502,15 @@ __global__ void __launch_bounds__(kThreads) k_extremes(Job j, Ws w) {
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
     amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
   }
-  __syncthreads();
+  consumers_sync();
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
     red_amin[warp] = amin;
   }
-  __syncthreads();
+  consumers_sync();
   if (threadIdx.x == 0) {
-    for (int q = 1; q < kWarps; q++) {
+    for (int q = 1; q < kClsConsumers; q++) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
       amin = min(amin, red_amin[q]);
     }
@@ -1042,17 +1120,36 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
   }
 }
 
+template <int DT>
+static void extremes_attr() {
+  static bool once = [] {
+    cudaFuncSetAttribute(k_extremes<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kExtSmem);
+    return true;
+  }();
+  (void)once;
+}
+
 int extremes_blocks_per_sm(int dtype) {
   int b = 0;
-  if (dtype == DT_F64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_F64>, kThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_I32>, kThreads, 0);
+  if (dtype == DT_F64) {
+    extremes_attr<DT_F64>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_F64>, kExtBlock, kExtSmem);
+  } else {
+    extremes_attr<DT_I32>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_I32>, kExtBlock, kExtSmem);
+  }
   return b > 0 ? b : 1;
 }
 
 int launch_extremes(const Job& j, const Ws& w, const Launch& L) {
   if (j.nchunk1 == 0) return 0;
-  if (j.dtype == DT_F64) k_extremes<DT_F64><<<j.nchunk1, kThreads, 0, L.stream>>>(j, w);
-  else k_extremes<DT_I32><<<j.nchunk1, kThreads, 0, L.stream>>>(j, w);
+  if (j.dtype == DT_F64) {
+    extremes_attr<DT_F64>();
+    k_extremes<DT_F64><<<j.nchunk1, kExtBlock, kExtSmem, L.stream>>>(j, w);
+  } else {
+    extremes_attr<DT_I32>();
+    k_extremes<DT_I32><<<j.nchunk1, kExtBlock, kExtSmem, L.stream>>>(j, w);
+  }
   return 1;
 }
 
