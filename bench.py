@@ -165,6 +165,120 @@ def run_reference(args):
     return 0
 
 
+def batched_bench(cch, torch, dev, stream, nsets):
+    """4096 int32 sets of log-uniform size in [256, 2^20] (square or disk by a
+    fair coin, seed 7): one cch_hull_batched launch sequence for all of them
+    against one cch_hull call per set, inputs resident; per-set results of the
+    two paths compared element-wise on the device."""
+    from paper_1508_05488_gb300 import inputs
+    pts, off = inputs.batched_i32(nsets, seed=7)
+    n_tot = int(off[-1])
+    d = torch.from_numpy(pts).to(dev)
+    del pts
+    idx_b = torch.empty(max(n_tot, 1), dtype=torch.int32, device=dev)
+    cnt_b = torch.empty(nsets, dtype=torch.int32, device=dev)
+    idx_c = torch.empty(max(n_tot, 1), dtype=torch.int32, device=dev)
+    cnt_c = torch.empty(nsets, dtype=torch.int32, device=dev)
+    offs = [int(v) for v in off]
+
+    def batched():
+        cch.hull_batched_async(d, off, idx_b, cnt_b, stream=stream)
+
+    def per_call(ev=None):
+        for s_ in range(nsets):
+            a, b = offs[s_], offs[s_ + 1]
+            if ev is not None:
+                ev[s_][0].record(stream)
+            cch.hull_async(d[a:b], idx_c[a:], cnt_c[s_:s_ + 1], stream=stream)
+            if ev is not None:
+                ev[s_][1].record(stream)
+
+    for _ in range(2):
+        batched()
+        per_call()
+    torch.cuda.synchronize()
+    same = bool(torch.equal(cnt_b, cnt_c))
+    if same:
+        for s_ in range(nsets):
+            c = int(cnt_b[s_])
+            if c > 0 and not torch.equal(idx_b[offs[s_]:offs[s_] + c], idx_c[offs[s_]:offs[s_] + c]):
+                same = False
+                break
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        batched()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / reps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsets)]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    per_call(ev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_calls = e0.elapsed_time(e1)
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+    return {"config": f"{nsets} int32 sets, sizes log-uniform in [256, 2^20] (seed 7), square or disk",
+            "points": n_tot, "hulls_per_s": nsets / (ms_batch * 1e-3), "ms_per_batch": ms_batch,
+            "per_call_hulls_per_s": nsets / (ms_calls * 1e-3), "per_call_ms_total": ms_calls,
+            "per_call_p50_ms": q(0.50), "per_call_p99_ms": q(0.99),
+            "speedup_vs_per_call": ms_calls / ms_batch, "identical_to_per_call": same}
+
+
+def serve_bench(cch, requests_per_load, pool_size=16):
+    """Poisson stream of float64 hull requests (sizes log-uniform in [1e3, 2e7],
+    square / disk / Gaussian / shell, seed 8) through the server: first the
+    closed-loop saturated rate, then offered loads of 0.5, 0.8 and 0.95 of it.
+    Every result is compared with the hull of the request computed alone."""
+    import numpy as np
+    from paper_1508_05488_gb300 import inputs
+    pool = [inputs.serve_request(i) for i in range(pool_size)]
+    alone = []
+    with cch.Server(np.float64) as srv:
+        for p in pool:
+            srv.submit(p)
+            got = []
+            while not got:
+                got = srv.poll()
+            alone.append(got[0][2])
+
+    def run(rate):
+        arrivals = inputs.poisson_arrivals(requests_per_load, rate) if rate else None
+        res, ok = {}, True
+        with cch.Server(np.float64) as srv:
+            t0 = time.perf_counter()
+            which = {}
+            for i in range(requests_per_load):
+                if arrivals is not None:
+                    wait = t0 + arrivals[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                which[srv.submit(pool[i % pool_size])] = i % pool_size
+                for t, st, h, lat in srv.poll():
+                    res[t] = (st, h)
+            while len(res) < requests_per_load:
+                for t, st, h, lat in srv.poll():
+                    res[t] = (st, h)
+                time.sleep(0.0002)
+            elapsed = time.perf_counter() - t0
+            stats = srv.stats()
+        for t, (st, h) in res.items():
+            ok &= st == 0 and np.array_equal(h, alone[which[t]])
+        return {"offered_hulls_per_s": rate, "hulls_per_s": requests_per_load / elapsed,
+                "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "identical_to_alone": bool(ok)}
+
+    sat = run(None)
+    loads = [run(f * sat["hulls_per_s"]) for f in (0.5, 0.8, 0.95)]
+    return {"config": f"{requests_per_load} float64 requests per load drawn from {pool_size} request sets "
+                      "(sizes log-uniform in [1e3, 2e7], square/disk/Gaussian/shell, seed 8); budget 64 GiB",
+            "mean_points_per_request": float(np.mean([len(p) for p in pool])),
+            "saturated": sat, "loads": loads}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +289,10 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=4_000_000)
     ap.add_argument("--ref-n", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-sets", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=96,
+                    help="requests per offered load (0: skip the serving measurement)")
     ap.add_argument("--kinds", default=",".join(KINDS),
                     help="comma-separated subset of square,disk,gauss (profiling runs)")
     args = ap.parse_args()
@@ -307,6 +425,10 @@ def main():
     if rank != 0:
         return 0
     cpu = None if args.no_cpu else cpu_baseline(host, args.cpu_n)
+    del dpts, outs
+    torch.cuda.empty_cache()
+    batched = None if args.no_batched else batched_bench(cch, torch, dev, stream, args.batched_sets)
+    serving = serve_bench(cch, args.serve_requests) if args.serve_requests > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -316,7 +438,7 @@ def main():
                    "hull_sizes": counts, "l2": "inputs larger than L2 (320 MB per set)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-        "gpu_launches": launches,
+        "gpu_launches": launches, "batched": batched, "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if dist:

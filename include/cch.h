@@ -173,7 +173,8 @@ int cch_hull_noalloc(const void *points, int64_t n, int dtype,
 /* Bytes of device scratch one cch_hull call of this size uses. */
 size_t cch_workspace_bytes(int64_t n, int dtype);
 
-/* Free every cached workspace (synchronises the device first). */
+/* Free every cached workspace and the servers' pooled pinned host buffers
+ * (synchronises the device first). */
 void cch_release_workspace(void);
 
 /* ------------------------------------------------------------ serving --

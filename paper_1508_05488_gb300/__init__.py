@@ -29,6 +29,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+class ServeConfig(ctypes.Structure):
+    """cch_serve_config."""
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("num_streams", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class Done(ctypes.Structure):
+    """cch_done."""
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("idx", ctypes.POINTER(ctypes.c_int32)), ("latency_ms", ctypes.c_double)]
+
+
 class CchError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = int(code)
@@ -71,8 +83,14 @@ def _load():
         lib.cch_launch_count.argtypes = []
         for name in ("cch_serve_create", "cch_serve_submit", "cch_serve_poll", "cch_serve_release",
                      "cch_serve_stats", "cch_serve_destroy"):
-            if hasattr(lib, name):
-                getattr(lib, name).restype = ctypes.c_int
+            getattr(lib, name).restype = ctypes.c_int
+        lib.cch_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
+        lib.cch_serve_submit.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.cch_serve_poll.argtypes = [vp, ctypes.POINTER(Done), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.cch_serve_release.argtypes = [vp, ctypes.c_uint64]
+        lib.cch_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        lib.cch_serve_destroy.argtypes = [vp]
         _lib = lib
         return lib
 
@@ -284,3 +302,62 @@ def workspace_bytes(n: int, dtype_code: int = CCH_F64) -> int:
 
 def release_workspace():
     _load().cch_release_workspace()
+
+
+class Server:
+    """Hull server (cch_serve_*): requests are admitted by a device-memory
+    budget and batched onto a pool of streams as they arrive.
+
+    ``submit`` copies a host ``[n, 2]`` array and returns a ticket; ``poll``
+    returns the finished requests as ``(ticket, status, hull, latency_ms)``
+    with ``hull`` a NumPy copy (the server's copy is released at once)."""
+
+    def __init__(self, dtype=np.float64, budget_bytes: int = 0, num_streams: int = 0, max_pending: int = 0,
+                 max_batch: int = 0):
+        self.dtype = np.dtype(dtype)
+        code = CCH_F64 if self.dtype == np.float64 else CCH_I32 if self.dtype == np.int32 else None
+        if code is None:
+            raise TypeError("points must be int32 or float64")
+        cfg = ServeConfig(budget_bytes, num_streams, max_pending, max_batch, code)
+        h = ctypes.c_void_p()
+        _check(_load().cch_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "cch_serve_create")
+        self._h = h
+
+    def submit(self, points) -> int:
+        p = np.ascontiguousarray(points, dtype=self.dtype)
+        if p.ndim != 2 or p.shape[1] != 2:
+            raise ValueError("points must be [n, 2]")
+        t = ctypes.c_uint64()
+        _check(_load().cch_serve_submit(self._h, p.ctypes.data, p.shape[0], ctypes.byref(t)), "cch_serve_submit")
+        return int(t.value)
+
+    def poll(self, max_results: int = 256):
+        arr = (Done * max_results)()
+        k = ctypes.c_int()
+        lib_ = _load()
+        _check(lib_.cch_serve_poll(self._h, arr, max_results, ctypes.byref(k)), "cch_serve_poll")
+        out = []
+        for i in range(k.value):
+            d = arr[i]
+            h = np.ctypeslib.as_array(d.idx, shape=(d.count,)).copy() if d.count > 0 else np.zeros(0, np.int32)
+            out.append((int(d.ticket), int(d.status), h, float(d.latency_ms)))
+            _check(lib_.cch_serve_release(self._h, d.ticket), "cch_serve_release")
+        return out
+
+    def stats(self) -> dict:
+        p50, p99, hps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(_load().cch_serve_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(hps),
+                                       ctypes.byref(n)), "cch_serve_stats")
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "hulls_per_s": hps.value, "finished": n.value}
+
+    def close(self):
+        if self._h:
+            _check(_load().cch_serve_destroy(self._h), "cch_serve_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

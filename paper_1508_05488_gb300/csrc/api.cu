@@ -483,6 +483,7 @@ size_t cch_workspace_bytes(int64_t n, int dtype) {
 void cch_release_workspace(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaDeviceSynchronize();
+  serve_release_pinned();
   for (auto& kv : g_ws) {
     Workspace* ws = kv.second;
     if (ws->dev) cudaFree(ws->dev);

@@ -741,5 +741,6 @@ int launch_chain(const Job& j, const Ws& w, const Launch& L);
 // stage extraction (cch_hull_stages)
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
 int extremes_blocks_per_sm(int dtype);
+void serve_release_pinned();   // free the server's pooled pinned host buffers
 
 }  // namespace cch
