@@ -32,8 +32,9 @@ WORKLOAD = ("20M float64 points each of: uniform in unit square (seed 2), unifor
 # only for the kernel source it was taken on.
 NCU_TRAFFIC = {
     # kernel: (bytes per point, source file, sha1 of that file when captured)
-    "k_classify": (262.58e6 / 16e6, "paper_1508_05488_gb300/csrc/k_round1.cu", "467cd4530d47e897addd6ce12231c4fac3e921d1"),
-    "k_extremes": (258.86e6 / 16e6, "paper_1508_05488_gb300/csrc/k_round1.cu", "467cd4530d47e897addd6ce12231c4fac3e921d1"),
+    # captured on 16M float64 points in the unit disk (profiles/k_classify_disk16M.md, k_extremes_disk16M.md)
+    "k_classify": ((258.666752e6 + 6.978816e6) / 16e6, "paper_1508_05488_gb300/csrc/k_round1.cu", "840d244202048c3bf86062db9dfecbddbb377dd5"),
+    "k_extremes": ((256.098816e6 + 3.633920e6) / 16e6, "paper_1508_05488_gb300/csrc/k_round1.cu", "840d244202048c3bf86062db9dfecbddbb377dd5"),
 }
 
 
