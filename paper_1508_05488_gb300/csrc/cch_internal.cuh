@@ -722,6 +722,34 @@ __device__ __forceinline__ void move_subslots(const Job& j, const Ws& w, const S
   }
 }
 
+// ------------------------------------------- programmatic dependent launch
+// The pipeline's kernels are launched with programmatic stream serialization:
+// a kernel may be set up while the previous kernel of its stream runs, and
+// its CTAs start as that kernel's CTAs exit.  Each of them first waits for
+// the previous kernel to complete and its writes to be visible (griddep_enter;
+// it returns at once when there is no such dependency), touching no memory
+// before, so only the launch latency and the tail of the previous kernel are
+// overlapped.  (Letting successors be scheduled from the start of a kernel,
+// griddepcontrol.launch_dependents, measured slower: their CTAs queue for
+// resources the running kernel holds.)
+__device__ __forceinline__ void griddep_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ------------------------------------------------------------ launchers
 // (defined in the kernel translation units, called from the API)
 struct Launch {

@@ -514,6 +514,7 @@ __device__ void big_spa(const Job& j, const Ws& w) {
 
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_big(Job j, Ws w) {
+  griddep_enter();
   const uint32_t total = w.ctr[CT_SORT_TOTAL];
   if (total == 0) {          // no multi-block set: one CTA plans the chains
     if (blockIdx.x == 0) plan_chain(j, w);

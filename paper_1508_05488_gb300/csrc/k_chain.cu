@@ -155,6 +155,7 @@ constexpr size_t chain_local_smem() {
 
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
+  griddep_enter();
   using P = typename PT<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   P* sp = reinterpret_cast<P*>(smem);
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
 
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_chain_merge(Job j, Ws w) {
+  griddep_enter();
   using P = typename PT<DT>::T;
   const int nseg = 4 * j.nsets;
   for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
@@ -337,6 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_merge(Job j, Ws w) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_output(Job j, Ws w) {
+  griddep_enter();
   __shared__ uint32_t sh_tile;
   __shared__ int sh_last;
   __shared__ uint32_t cnt[kOutItems][kWarps];
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__(kThreads) k_output(Job j, Ws w) {
 
 // ---------------------------------------------------- stage extraction
 __global__ void k_extract_spa(Job j, Ws w, int32_t* spa_idx) {
+  griddep_enter();
   const SetDesc sd = get_set(j, 0);
   const SetCtl& c = w.ctl[0];
   uint32_t o = 0;
@@ -449,7 +453,7 @@ __global__ void k_extract_spa(Job j, Ws w, int32_t* spa_idx) {
 }
 
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st) {
-  k_extract_spa<<<256, kThreads, 0, st>>>(j, w, spa_idx);
+  launch_pdl(k_extract_spa, 256, kThreads, 0, st, j, w, spa_idx);
 }
 
 int launch_chain(const Job& j, const Ws& w, const Launch& L) {
@@ -464,8 +468,8 @@ int launch_chain(const Job& j, const Ws& w, const Launch& L) {
       return true;
     }();
     (void)once;
-    k_chain_local<DT_F64><<<grid, kThreads, sm, L.stream>>>(j, w);
-    k_chain_merge<DT_F64><<<gridm, kThreads, 0, L.stream>>>(j, w);
+    launch_pdl(k_chain_local<DT_F64>, grid, kThreads, sm, L.stream, j, w);
+    launch_pdl(k_chain_merge<DT_F64>, gridm, kThreads, 0, L.stream, j, w);
   } else {
     constexpr size_t sm = chain_local_smem<DT_I32>();
     static bool once = [] {
@@ -473,10 +477,10 @@ int launch_chain(const Job& j, const Ws& w, const Launch& L) {
       return true;
     }();
     (void)once;
-    k_chain_local<DT_I32><<<grid, kThreads, sm, L.stream>>>(j, w);
-    k_chain_merge<DT_I32><<<gridm, kThreads, 0, L.stream>>>(j, w);
+    launch_pdl(k_chain_local<DT_I32>, grid, kThreads, sm, L.stream, j, w);
+    launch_pdl(k_chain_merge<DT_I32>, gridm, kThreads, 0, L.stream, j, w);
   }
-  k_output<<<grid, kThreads, 0, L.stream>>>(j, w);
+  launch_pdl(k_output, grid, kThreads, 0, L.stream, j, w);
   return 3;
 }
 

@@ -327,6 +327,7 @@ __device__ __forceinline__ void consumers_sync() {
 // every tile, so every thread meets its points in increasing index order.
 template <int DT>
 __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
+  griddep_enter();
   using P = typename PointT<DT>::T;
   constexpr int PB = (int)sizeof(P);
   constexpr int TILE = kClsTileBytes / PB;
@@ -522,6 +523,7 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
 
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
+  griddep_enter();
   using P = typename PointT<DT>::T;
   __shared__ uint32_t tb[4][kStairB];
   __shared__ int last;
@@ -758,6 +760,7 @@ struct WarpParams {
 // sub-slot) -- no block-wide barrier on the per-tile path.
 template <int DT>
 __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
+  griddep_enter();
   using P = typename PointT<DT>::T;
   constexpr int PB = (int)sizeof(P);
   constexpr int TILE = kClsTileBytes / PB;
@@ -1019,6 +1022,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
 // most kSmallMax) and the multi-block sort, and plans both.
 
 __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
+  griddep_enter();
   constexpr int kSubPerWarp = kPlanTiles * kClsConsumers / kWarps;
   __shared__ uint32_t sh_tot[4], sh_cpre[4];
   __shared__ uint32_t wtot[kWarps][4];
@@ -1145,23 +1149,23 @@ int launch_extremes(const Job& j, const Ws& w, const Launch& L) {
   if (j.nchunk1 == 0) return 0;
   if (j.dtype == DT_F64) {
     extremes_attr<DT_F64>();
-    k_extremes<DT_F64><<<j.nchunk1, kExtBlock, kExtSmem, L.stream>>>(j, w);
+    launch_pdl(k_extremes<DT_F64>, j.nchunk1, kExtBlock, kExtSmem, L.stream, j, w);
   } else {
     extremes_attr<DT_I32>();
-    k_extremes<DT_I32><<<j.nchunk1, kExtBlock, kExtSmem, L.stream>>>(j, w);
+    launch_pdl(k_extremes<DT_I32>, j.nchunk1, kExtBlock, kExtSmem, L.stream, j, w);
   }
   return 1;
 }
 
 int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
   if (j.nchunk3 == 0) return 0;
-  if (j.dtype == DT_F64) k_stairs<DT_F64><<<j.nchunk3, kThreads, 0, L.stream>>>(j, w);
-  else k_stairs<DT_I32><<<j.nchunk3, kThreads, 0, L.stream>>>(j, w);
+  if (j.dtype == DT_F64) launch_pdl(k_stairs<DT_F64>, j.nchunk3, kThreads, 0, L.stream, j, w);
+  else launch_pdl(k_stairs<DT_I32>, j.nchunk3, kThreads, 0, L.stream, j, w);
   return 1;
 }
 
 int launch_gather(const Job& j, const Ws& w, const Launch& L) {
-  k_gather<<<j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream>>>(j, w);
+  launch_pdl(k_gather, j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream, j, w);
   return 1;
 }
 
@@ -1174,14 +1178,14 @@ int launch_classify(const Job& j, const Ws& w, const Launch& L) {
       return true;
     }();
     (void)once;
-    k_classify<DT_F64><<<grid, kClsBlock, cls_smem_bytes<DT_F64>(), L.stream>>>(j, w);
+    launch_pdl(k_classify<DT_F64>, grid, kClsBlock, cls_smem_bytes<DT_F64>(), L.stream, j, w);
   } else {
     static bool once = [] {
       cudaFuncSetAttribute(k_classify<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT_I32>());
       return true;
     }();
     (void)once;
-    k_classify<DT_I32><<<grid, kClsBlock, cls_smem_bytes<DT_I32>(), L.stream>>>(j, w);
+    launch_pdl(k_classify<DT_I32>, grid, kClsBlock, cls_smem_bytes<DT_I32>(), L.stream, j, w);
   }
   return 1;
 }

@@ -201,6 +201,7 @@ __device__ __forceinline__ void prefix_min_excl(uint32_t* t, uint32_t seed, uint
 
 template <int DT>
 __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
+  griddep_enter();
   using P = typename std::conditional<DT == DT_F64, double2, int2>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* vminA = reinterpret_cast<uint32_t*>(smem);                           // table A (padded)
@@ -603,14 +604,14 @@ int launch_small(const Job& j, const Ws& w, const Launch& L) {
       return true;
     }();
     (void)once;
-    k_small<DT_F64><<<grid, kSmThreads, kSmSmem, L.stream>>>(j, w);
+    launch_pdl(k_small<DT_F64>, grid, kSmThreads, kSmSmem, L.stream, j, w);
   } else {
     static bool once = [] {
       cudaFuncSetAttribute(k_small<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmSmem);
       return true;
     }();
     (void)once;
-    k_small<DT_I32><<<grid, kSmThreads, kSmSmem, L.stream>>>(j, w);
+    launch_pdl(k_small<DT_I32>, grid, kSmThreads, kSmSmem, L.stream, j, w);
   }
   return 1;
 }
