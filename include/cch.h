@@ -151,6 +151,15 @@ int cch_profile_read(double *stage_ms, int max_stages, int64_t *calls);
 uint64_t cch_launch_count(void);
 
 /*
+ * Self-test of the device-side failure path: one kernel waits on a device
+ * flag that nothing sets, with the same bounded wait every kernel of the
+ * library uses, and must give up and report.  Writes to *status_dev (device
+ * int32) the status the wait recorded -- CCH_ERR_TIMEOUT when the path works
+ * -- asynchronously on `stream`.  The context stays usable afterwards.
+ */
+int cch_selftest_wait(int32_t *status_dev, void *stream);
+
+/*
  * cch_hull without any device-memory allocation, for callers that cannot
  * call cudaMalloc: code running under a CUDA graph capture that forbids
  * allocation, real-time or embedded callers whose device footprint is fixed

@@ -81,6 +81,8 @@ def _load():
         lib.cch_profile_read.argtypes = [vp, ctypes.c_int, vp]
         lib.cch_launch_count.restype = ctypes.c_uint64
         lib.cch_launch_count.argtypes = []
+        lib.cch_selftest_wait.restype = ctypes.c_int
+        lib.cch_selftest_wait.argtypes = [vp, vp]
         for name in ("cch_serve_create", "cch_serve_submit", "cch_serve_poll", "cch_serve_release",
                      "cch_serve_stats", "cch_serve_destroy"):
             getattr(lib, name).restype = ctypes.c_int

@@ -472,6 +472,38 @@ int cch_profile_read(double* stage_ms, int max_stages, int64_t* calls) {
 
 uint64_t cch_launch_count(void) { return g_launches.load(); }
 
+namespace cch {
+namespace {
+// One thread waits on a flag that nothing sets, with the library's bounded
+// wait; the error word it records is the result.
+__global__ void k_selftest_wait(uint32_t* words, int32_t* status) {
+  uint32_t* flag = words + CT_COUNT;
+  uint32_t spins = 0;
+  while (ld_acq_u32(flag) == 0)
+    if (!spin_step(spins, words)) break;
+  *status = (int32_t)ld_acq_u32(words + CT_ERR);
+}
+}  // namespace
+}  // namespace cch
+
+int cch_selftest_wait(int32_t* status_dev, void* stream) {
+  if (!status_dev) return CCH_ERR_INVALID;
+  static uint32_t* words = nullptr;           // CT_COUNT error words + the flag
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!words && cudaMalloc(&words, sizeof(uint32_t) * (CT_COUNT + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      words = nullptr;
+      return CCH_ERR_NOMEM;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(words, 0, sizeof(uint32_t) * (CT_COUNT + 1), st) != cudaSuccess) return CCH_ERR_CUDA;
+  k_selftest_wait<<<1, 1, 0, st>>>(words, status_dev);
+  g_launches += 1;
+  return cudaGetLastError() == cudaSuccess ? CCH_OK : CCH_ERR_CUDA;
+}
+
 size_t cch_workspace_bytes(int64_t n, int dtype) {
   if (n < 0 || (dtype != CCH_I32 && dtype != CCH_F64)) return 0;
   int target = 1216;

@@ -231,6 +231,19 @@ def test_host_errors_return_codes():
     assert lib.cch_hull(x.data_ptr(), 4, 2, None, c.data_ptr(), None) == -1
 
 
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """The device-side failure path: a wait on a flag nothing sets gives up
+    within its bound and reports CCH_ERR_TIMEOUT; later calls still work."""
+    import time
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    t0 = time.time()
+    assert cch.lib().cch_selftest_wait(st.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 10.0
+    assert int(st.item()) == -7
+    check(inputs.disk_f64(50_000, 9))
+
+
 def test_repeated_calls_and_streams_are_independent():
     a = inputs.disk_f64(200_000, 31)
     b = inputs.square_i32(300_000, 32)
