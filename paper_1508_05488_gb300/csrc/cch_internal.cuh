@@ -47,13 +47,19 @@ __host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048
 // sample of the set.
 constexpr int kStairB = 1024;          // buckets per region
 constexpr int64_t kStairSample = int64_t(1) << 20;   // sample points per set (the last ones)
-constexpr int kStairChunk = 8192;      // sample points per CTA
+constexpr int kStairChunk = 4096;      // sample points per CTA
+constexpr int64_t kStairMin = 8192;    // smallest sample of a set
 constexpr int kPlanTiles = 64;         // a2 tiles per survivor-count chunk (one gather CTA)
+// a1 reads the last kL2KeepBytes of every set without the evict-first hint,
+// so that they are still in L2 when k_stairs samples them (its sample is the
+// set's tail) and when a2 starts (a2 hands out its tiles from the last to the
+// first).
+constexpr int64_t kL2KeepBytes = int64_t(48) << 20;
 // Sample of a set: its last m points (the most recently streamed by a1),
 // m = min(n, 2^20, max(8192, n / 16)).
 __host__ __device__ inline int64_t stairs_sample(int64_t n) {
   int64_t m = n / 16;
-  if (m < kStairChunk) m = kStairChunk;
+  if (m < kStairMin) m = kStairMin;
   if (m > kStairSample) m = kStairSample;
   return m < n ? m : n;
 }
@@ -595,6 +601,15 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+// The same copy with an L2 evict-first policy: for input that a1 and a2
+// stream once, so that it does not push the small survivor buffers, tables,
+// control words and kernel code of the later steps out of L2.
+__device__ __forceinline__ void tma_load_1d_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

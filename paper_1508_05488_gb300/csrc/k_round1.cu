@@ -389,7 +389,10 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
       if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
       if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
       mbar_arrive_tx(&full[slot], bytes);
-      if (bytes) tma_load_1d(dst, src + head * PB, bytes, &full[slot]);
+      if (bytes) {
+        if ((sd.n - i0) * PB <= kL2KeepBytes) tma_load_1d(dst, src + head * PB, bytes, &full[slot]);
+        else tma_load_1d_stream(dst, src + head * PB, bytes, &full[slot]);
+      }
       issued = it + 1;
     }
     if (!ok) {
@@ -796,7 +799,10 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
         if (!ok) break;
         fence_async_smem();
       }
-      const uint32_t t = atomicAdd(w.ctr + CT_CLS_TILE, 1u);
+      // tiles from the last to the first: the first ones are still in L2
+      // from a1
+      const uint32_t tc = atomicAdd(w.ctr + CT_CLS_TILE, 1u);
+      const uint32_t t = tc < (uint32_t)j.ntile2 ? (uint32_t)j.ntile2 - 1u - tc : tc;
       st_tile[slot] = (int)t;
       if (t >= (uint32_t)j.ntile2) {
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&full[slot])) : "memory");
@@ -825,7 +831,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
       if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
       if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
       mbar_arrive_tx(&full[slot], bytes);
-      if (bytes) tma_load_1d(dst, src + head * PB, bytes, &full[slot]);
+      if (bytes) tma_load_1d_stream(dst, src + head * PB, bytes, &full[slot]);
       issued = it + 1;
     }
     if (!ok) {
