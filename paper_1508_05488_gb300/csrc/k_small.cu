@@ -28,6 +28,15 @@
 //  3. SPA proper: exclusive prefix minimum of the exact SPA value over the
 //     sorted order, seeded with the first extreme; the survivors go, in
 //     order, to the region's chain slots.
+//  Record path.  The candidates sit in index order, the sort visits them in
+//  key order, so every later read of a candidate's key or SPA value is a
+//  random gather from L2.  The keep test reads both in order anyway: it
+//  also writes each kept candidate's record (key, SPA value, candidate
+//  number), in keep order, to the (by then unused) second record buffers.
+//  When at most kRecMax candidates are kept and the counting path applies,
+//  the records come back into shared memory in one sequential copy, and
+//  steps 2a and 3 read only shared memory; the output gathers only the
+//  survivors' point indices.
 #include <type_traits>
 
 #include "cch_internal.cuh"
@@ -40,6 +49,7 @@ constexpr int kSmItems = kSmallMax / kSmThreads;   // at most 32 candidates per 
 constexpr int kFineB = 16384;                      // fine buckets of the sort key per region
 constexpr int kFineB2 = 8192;                      // fine buckets of the SPA value per region
 constexpr int kOccMax = 32;                        // largest bucket the counting path ranks
+constexpr int kRecMax = 4096;                      // most kept candidates the record path holds
 // Dynamic shared memory, overlays of one 200 KB block (tables padded by one
 // word in 32):
 //   filter         table A u32 | table B u32 | kept-candidate list u16 (its
@@ -47,10 +57,15 @@ constexpr int kOccMax = 32;                        // largest bucket the countin
 //                  u16 pairs, over sposB and the histograms
 //   counting path  bucket members u16 from 0 (tables dead by then)
 //   radix path     [0, 128K) keys u64 (tables, list and counts dead by then)
+//   record path    membR u16 [0, 8K) | rk u64 [8K, 40K) | rv u64 [40K, 72K) |
+//                  ri u32 [72K, 88K): the kept candidates' records (sort key,
+//                  SPA value, candidate number) in keep order (at most
+//                  kRecMax; the tables are dead by then)
 //   both           [128K, 160K) sposA u16 (sorted positions) | [160K, 192K)
 //                  sposB u16 | [192K, 200K) per-warp digit histograms;
 //                  step 3 overwrites [0, 128K) with SPA values in sorted order
-//                  and lists the survivors in the free position buffer
+//                  (not on the record path) and lists the survivors in the
+//                  free position buffer
 constexpr size_t kSmSmem = (size_t)kSmallMax * (8 + 2 + 2) + (size_t)kSmWarps * 256 * 2;
 constexpr int kPadA = kFineB + kFineB / 32;       // padded table words
 constexpr int kPadB = kFineB2 + kFineB2 / 32;
@@ -59,6 +74,8 @@ static_assert((size_t)(kPadA + kPadB) * 4 + (size_t)kSmallMax * 2 <= (size_t)kSm
               "tables and the kept list end before the second position buffer");
 static_assert((size_t)kPadC * 4 <= (size_t)kSmallMax * 2 + (size_t)kSmWarps * 256 * 2,
               "bucket counts fit the second position buffer and the histograms");
+static_assert((size_t)kRecMax * (2 + 8 + 8 + 4) <= (size_t)(kPadA + kPadB) * 4,
+              "records end before the kept-candidate list");
 
 template <int DT>
 __device__ __forceinline__ uint64_t spa_value_of(const typename std::conditional<DT == DT_F64, double2, int2>::type& p,
@@ -289,7 +306,11 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
     prefix_min_excl<kFineB2 / kSmThreads>(vminB, 0xFFFFFFFFu, wmx);
     __syncthreads();
     // keep test: kept candidates are listed (any order), marked in keepw
-    // (index order) and counted per bucket of table A
+    // (index order), counted per bucket of table A and their records
+    // written in list order
+    uint64_t* rkG = w.keyB + sd.off + rbase;
+    uint64_t* rvG = w.spvB + sd.off + rbase;
+    uint32_t* riG = w.valB + sd.off + rbase;
 #pragma unroll 1
     for (uint32_t i0 = 0; i0 < m; i0 += kSmThreads * 8) {
       uint64_t kk[8], va[8];
@@ -318,8 +339,10 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
           }
           base = __shfl_sync(0xFFFFFFFFu, base, 0);
           if (keep) {
-            klist[base + __popc(bal & lt_mask)] = (uint16_t)i;
+            const uint32_t pos = base + __popc(bal & lt_mask);
+            klist[pos] = (uint16_t)i;
             atomicAdd(&bcnt[pad32(b >> 1)], 1u << ((b & 1u) * 16u));
+            if (pos < kRecMax) { rkG[pos] = kk[u]; rvG[pos] = va[u]; riG[pos] = i; }
           }
         }
       }
@@ -364,7 +387,50 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
     __syncthreads();
 
     uint16_t* pin = sposA;
-    if (maxocc <= kOccMax) {
+    // record path: pin holds record numbers (keep order), else candidate
+    // numbers (index order)
+    const bool rec = maxocc <= kOccMax && m2 <= kRecMax;
+    uint16_t* membR = reinterpret_cast<uint16_t*>(smem);
+    uint64_t* rk = reinterpret_cast<uint64_t*>(smem + (size_t)kRecMax * 2);
+    uint64_t* rv = rk + kRecMax;
+    uint32_t* ri = reinterpret_cast<uint32_t*>(rv + kRecMax);
+    if (rec) {
+      // ---- 2a'. counting path on the records ----------------------------
+      for (uint32_t t = tid; t < m2; t += kSmThreads) {
+        rk[t] = rkG[t];
+        rv[t] = rvG[t];
+        ri[t] = riG[t];
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (uint32_t t = tid; t < m2; t += kSmThreads) {
+        const uint32_t b = fa.bucket<DT>(rk[t]);
+        const uint32_t sh = (b & 1u) * 16u;
+        const uint32_t old = atomicAdd(&bcnt[pad32(b >> 1)], 1u << sh);
+        membR[(old >> sh) & 0xFFFFu] = (uint16_t)t;
+      }
+      __syncthreads();
+      // rank within the bucket by (key, index)
+#pragma unroll 1
+      for (uint32_t t = tid; t < m2; t += kSmThreads) {
+        const uint32_t x = membR[t];
+        const uint64_t ki = rk[x];
+        const uint32_t ii = ri[x];
+        const uint32_t b = fa.bucket<DT>(ki);
+        const uint32_t en = (bcnt[pad32(b >> 1)] >> ((b & 1u) * 16u)) & 0xFFFFu;
+        const uint32_t st = b ? (bcnt[pad32((b - 1) >> 1)] >> (((b - 1) & 1u) * 16u)) & 0xFFFFu : 0u;
+        uint32_t rkx = 0;
+        for (uint32_t p = st; p < en; p++) {
+          const uint32_t y = membR[p];
+          if (y != x) {
+            const uint64_t kj = rk[y];
+            rkx += (kj < ki) || (kj == ki && ri[y] < ii);
+          }
+        }
+        sposA[st + rkx] = (uint16_t)x;
+      }
+      __syncthreads();
+    } else if (maxocc <= kOccMax) {
       // ---- 2a. counting path ------------------------------------------
       // scatter by bucket: the starts become cursors, then bucket ends
 #pragma unroll 1
@@ -507,20 +573,27 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
     const int per2 = (int)((m2 + kSmThreads - 1) / kSmThreads);
     const uint32_t i0 = tid * (uint32_t)per2;
     uint64_t tmin = ~0ull;
-#pragma unroll 1
-    for (int k0 = 0; k0 < per2; k0 += 4) {
-      uint64_t va[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const uint32_t i = i0 + k0 + u;
-        va[u] = (k0 + u < per2 && i < m2) ? vv[pin[i]] : ~0ull;
+    if (rec) {
+      for (int k = 0; k < per2; k++) {
+        const uint32_t i = i0 + k;
+        if (i < m2) tmin = min(tmin, rv[pin[i]]);
       }
+    } else {
+#pragma unroll 1
+      for (int k0 = 0; k0 < per2; k0 += 4) {
+        uint64_t va[4];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const uint32_t i = i0 + k0 + u;
-        if (k0 + u < per2 && i < m2) {
-          skey[i] = va[u];
-          tmin = min(tmin, va[u]);
+        for (int u = 0; u < 4; u++) {
+          const uint32_t i = i0 + k0 + u;
+          va[u] = (k0 + u < per2 && i < m2) ? vv[pin[i]] : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const uint32_t i = i0 + k0 + u;
+          if (k0 + u < per2 && i < m2) {
+            skey[i] = va[u];
+            tmin = min(tmin, va[u]);
+          }
         }
       }
     }
@@ -540,7 +613,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
     for (int k = 0; k < per2; k++) {
       const uint32_t i = i0 + k;
       if (i >= m2) break;
-      const uint64_t v = skey[i];
+      const uint64_t v = rec ? rv[pin[i]] : skey[i];
       if (v <= run) { keep2 |= 1u << k; n2++; }
       run = min(run, v);
     }
@@ -566,24 +639,45 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
     {
       const int64_t cb = chain_base(sd, s, c, r) + 1;
       P* cp = reinterpret_cast<P*>(w.cpts);
+      if (rec) {
 #pragma unroll 1
-      for (uint32_t t0 = 0; t0 < tot; t0 += kSmThreads * 4) {
-        uint32_t idx[4];
-        uint64_t kk[4], va[4];
+        for (uint32_t t0 = 0; t0 < tot; t0 += kSmThreads * 8) {
+          uint32_t idx[8];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const uint32_t t = t0 + u * kSmThreads + tid;
-          const uint32_t p = t < tot ? surv[t] : 0u;
-          idx[u] = t < tot ? vin[p] & kIdxMask : 0u;
-          kk[u] = t < tot ? kin[p] : 0ull;
-          va[u] = t < tot ? vv[p] : 0ull;
+          for (int u = 0; u < 8; u++) {
+            const uint32_t t = t0 + u * kSmThreads + tid;
+            idx[u] = t < tot ? vin[ri[surv[t]]] & kIdxMask : 0u;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; u++) {
+            const uint32_t t = t0 + u * kSmThreads + tid;
+            if (t < tot) {
+              const uint32_t p = surv[t];
+              w.cidx[cb + t] = idx[u];
+              cp[cb + t] = point_from_keys<DT>(rk[p], rv[p], r);
+            }
+          }
         }
+      } else {
+#pragma unroll 1
+        for (uint32_t t0 = 0; t0 < tot; t0 += kSmThreads * 4) {
+          uint32_t idx[4];
+          uint64_t kk[4], va[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const uint32_t t = t0 + u * kSmThreads + tid;
-          if (t < tot) {
-            w.cidx[cb + t] = idx[u];
-            cp[cb + t] = point_from_keys<DT>(kk[u], va[u], r);
+          for (int u = 0; u < 4; u++) {
+            const uint32_t t = t0 + u * kSmThreads + tid;
+            const uint32_t p = t < tot ? surv[t] : 0u;
+            idx[u] = t < tot ? vin[p] & kIdxMask : 0u;
+            kk[u] = t < tot ? kin[p] : 0ull;
+            va[u] = t < tot ? vv[p] : 0ull;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const uint32_t t = t0 + u * kSmThreads + tid;
+            if (t < tot) {
+              w.cidx[cb + t] = idx[u];
+              cp[cb + t] = point_from_keys<DT>(kk[u], va[u], r);
+            }
           }
         }
       }
