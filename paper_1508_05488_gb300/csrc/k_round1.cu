@@ -524,11 +524,38 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
 
 // ------------------------------------------------------------ stairs
 
+// Padded index of a stairs table word (one spare word in 32): 64 threads
+// reading 16 consecutive words each hit 32 different banks.
+__device__ __forceinline__ int stair_pad(int b) { return b + (b >> 5); }
+
+// Exclusive minimum of `v` over the lower threads of the same 64-thread
+// region group (threads 64r .. 64r+63, two warps); sw holds one word per
+// warp.  Ends with the CTA synchronised.
+__device__ __forceinline__ uint32_t region_excl_min(uint32_t v, uint32_t* sw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x = min(x, y);
+  }
+  if (lane == 31) sw[warp] = x;
+  __syncthreads();
+  uint32_t ex = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+  if (lane == 0) ex = 0xFFFFFFFFu;
+  if (warp & 1) ex = min(ex, sw[warp - 1]);
+  __syncthreads();
+  return ex;
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
-  __shared__ uint32_t tb[4][kStairB];
+  constexpr int kTb = kStairB + kStairB / 32;   // padded table (one spare word in 32)
+  static_assert(kThreads == 4 * 64 && kStairB == 64 * 16, "64 threads x 16 buckets per region");
+  __shared__ uint32_t tb[4][kTb];
+  __shared__ uint32_t sw[kWarps];
   __shared__ int last;
   const int chunk = blockIdx.x;
   int s = 0;
@@ -546,7 +573,7 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   float lo[4], hi[4], sc[4];
 #pragma unroll
   for (int r = 0; r < 4; r++) { lo[r] = c.slo[r]; hi[r] = c.shi[r]; sc[r] = c.sscale[r]; }
-  for (int i = threadIdx.x; i < 4 * kStairB; i += kThreads) (&tb[0][0])[i] = 0xFFFFFFFFu;
+  for (int i = threadIdx.x; i < 4 * kTb; i += kThreads) (&tb[0][0])[i] = 0xFFFFFFFFu;
   __syncthreads();
 
   const int64_t m = stairs_sample(sd.n);
@@ -578,7 +605,7 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
       for (int r = 0; r < 4; r++) {
         float su = sort_u(X, Y, r);
         if (su >= lo[r] && su <= hi[r])
-          atomicMin(&tb[r][stair_bucket(su, lo[r], sc[r])], cmp_key_hi<DT>(v[u], r));
+          atomicMin(&tb[r][stair_pad(stair_bucket(su, lo[r], sc[r]))], cmp_key_hi<DT>(v[u], r));
       }
     }
   }
@@ -590,10 +617,22 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
       atomicMax((unsigned long long*)&w.ctl[s].dq[q], (unsigned long long)~dq[q]);
   }
   __syncthreads();
+  // Merge into the set's tables.  The tables only ever feed exclusive prefix
+  // minima over lower buckets, so an entry that is not below this CTA's own
+  // minimum over the lower buckets changes nothing (the lower bucket already
+  // holds a value at least as small): only the CTA's staircase steps go out.
+  // 64 threads per region, 16 consecutive buckets each.
   uint32_t* g = w.stairs + (size_t)s * 4 * kStairB;
-  for (int i = threadIdx.x; i < 4 * kStairB; i += kThreads) {
-    uint32_t v = (&tb[0][0])[i];
-    if (v != 0xFFFFFFFFu) atomicMin(g + i, v);
+  const int rr = threadIdx.x >> 6, ru = threadIdx.x & 63;
+  {
+    uint32_t loc[16];
+    uint32_t mn = 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < 16; q++) { loc[q] = tb[rr][stair_pad(ru * 16 + q)]; mn = min(mn, loc[q]); }
+    uint32_t ex = region_excl_min(mn, sw);
+#pragma unroll
+    for (int q = 0; q < 16; q++)
+      if (loc[q] < ex) { atomicMin(g + rr * kStairB + ru * 16 + q, loc[q]); ex = loc[q]; }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -603,6 +642,14 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // Last CTA of the set.  The table loads and the dominance box's loads are
+  // issued together.
+  uint4 tv[4];
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(g + rr * kStairB + ru * 16);
+#pragma unroll
+    for (int q = 0; q < 4; q++) tv[q] = __ldcg(src + q);
+  }
   // dominance box: a point strictly inside it is strictly beaten in all four
   // quadrants by sample points (Qll lower-left of it, Qlr lower-right, ...)
   if (threadIdx.x == 0) {
@@ -620,33 +667,27 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
     }
   }
   // exclusive prefix minimum per region, seeded with the first extreme
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 4) {
-    const int r = warp;
-    P e;
-    if constexpr (DT == DT_F64) { e.x = c.ex[r]; e.y = c.ey[r]; }
-    else { e.x = (int)c.ex[r]; e.y = (int)c.ey[r]; }
-    uint32_t run = cmp_key_hi<DT>(e, r);
-    uint32_t* t = g + r * kStairB;
-    constexpr int per = kStairB / 32;
-    uint32_t loc[per];
+  {
+    uint32_t loc[16];
+#pragma unroll
+    for (int q = 0; q < 4; q++) { loc[4 * q] = tv[q].x; loc[4 * q + 1] = tv[q].y; loc[4 * q + 2] = tv[q].z; loc[4 * q + 3] = tv[q].w; }
     uint32_t mn = 0xFFFFFFFFu;
 #pragma unroll
-    for (int q = 0; q < per; q++) { loc[q] = *(volatile uint32_t*)(t + lane * per + q); mn = min(mn, loc[q]); }
-    uint32_t x = mn;
+    for (int q = 0; q < 16; q++) mn = min(mn, loc[q]);
+    P e;
+    if constexpr (DT == DT_F64) { e.x = c.ex[rr]; e.y = c.ey[rr]; }
+    else { e.x = (int)c.ex[rr]; e.y = (int)c.ey[rr]; }
+    uint32_t ex = min(region_excl_min(mn, sw), cmp_key_hi<DT>(e, rr));
+    uint4 o[4];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x = min(x, y);
+    for (int q = 0; q < 16; q++) {
+      const uint32_t v = loc[q];
+      (&o[q >> 2].x)[q & 3] = ex;
+      ex = min(ex, v);
     }
-    uint32_t ex = __shfl_up_sync(0xFFFFFFFFu, x, 1);
-    if (lane == 0) ex = 0xFFFFFFFFu;
-    ex = min(ex, run);
+    uint4* dst = reinterpret_cast<uint4*>(g + rr * kStairB + ru * 16);
 #pragma unroll
-    for (int q = 0; q < per; q++) {
-      t[lane * per + q] = ex;
-      ex = min(ex, loc[q]);
-    }
+    for (int q = 0; q < 4; q++) dst[q] = o[q];
   }
 }
 
