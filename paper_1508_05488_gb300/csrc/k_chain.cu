@@ -107,6 +107,15 @@ struct GlobAcc {
   }
 };
 
+// Asynchronous global -> shared copy of B (8 or 16) bytes, both B-aligned.
+template <int B>
+__device__ __forceinline__ void cp_async_copy(void* dst, const void* src) {
+  static_assert(B == 8 || B == 16, "cp.async copies 8 or 16 bytes here");
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (B == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(d), "l"(src) : "memory");
+}
+
 constexpr int kPeelRounds = 48;   // peeling rounds before the stack-and-merge fallback
 
 // Exclusive prefix sum of one value per thread over the CTA; sh[kWarps]
@@ -182,20 +191,28 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
     const int64_t cb = chain_base(sd, s, c, r);
     const uint32_t p0 = lb * kChainBlk;
     const int m = (int)min((uint32_t)kChainBlk, L - p0);
+    // the block's points straight into shared memory (all copies in
+    // flight at once); the chain's two extremes come from the set's record
     for (int i = threadIdx.x; i < m; i += kThreads) {
-      uint32_t p = p0 + i;
-      P v;
-      if (p == 0 || p == L - 1) {
-        int k = p == 0 ? r : ((r + 1) & 3);
+      const uint32_t p = p0 + i;
+      if (p != 0 && p != L - 1) cp_async_copy<sizeof(P)>(&sp[i], &cp[cb + p]);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (threadIdx.x < 2) {
+      const uint32_t p = threadIdx.x == 0 ? 0u : L - 1;
+      if (p >= p0 && p < p0 + (uint32_t)m) {
+        const int k = p == 0 ? r : ((r + 1) & 3);
+        P v;
         if constexpr (DT == DT_F64) { v.x = c.ex[k]; v.y = c.ey[k]; }
         else { v.x = (int)c.ex[k]; v.y = (int)c.ey[k]; }
         cp[cb + p] = v;
         w.cidx[cb + p] = c.eidx[k];
-      } else {
-        v = cp[cb + p];
+        sp[p - p0] = v;
       }
-      sp[i] = v;
-      if constexpr (DT == DT_F64) sf[i] = f64_split4(v);
+    }
+    if constexpr (DT == DT_F64) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += kThreads) sf[i] = f64_split4(sp[i]);
     }
     if (threadIdx.x == 0 && p0 > 0) pred = cp[cb + p0 - 1];
     __syncthreads();
