@@ -286,6 +286,36 @@ def serve_bench(cch, requests_per_load, pool_size=16):
 SURVIVOR_SIZES = (100_000, 200_000, 500_000, 1_000_000, 2_000_000, 5_000_000, 10_000_000, 20_000_000)
 
 
+def f32soa_bench(cch, torch, host_square, reps):
+    """The paper's input form (Fig. 6: two float32 coordinate vectors): the
+    square set rounded to float32, through cch_hull_f32soa (exact widening
+    to float64, then the same pipeline), inputs resident on the device."""
+    import numpy as np
+    p32 = host_square.astype(np.float32)
+    x = torch.from_numpy(np.ascontiguousarray(p32[:, 0])).cuda()
+    y = torch.from_numpy(np.ascontiguousarray(p32[:, 1])).cuda()
+    n = x.shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        cch.hull_f32soa_async(x, y, idx, cnt)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        cch.hull_f32soa_async(x, y, idx, cnt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    h = int(cnt.item())
+    ref = cch.hull(torch.stack([x, y], 1).double())
+    same = h == ref.shape[0] and bool(torch.equal(idx[:h], ref))
+    del x, y, idx
+    return {"config": f"{n} float32 points of the square set as two coordinate vectors", "value": n / ms / 1e3,
+            "unit": "Mpoints/s", "ms_per_hull": ms, "hull_size": h, "identical_to_float64_path": same}
+
+
 def survivors(kinds, sizes, reps):
     """Points left after each round of discarding against n (Sec. 3.3, Fig. 11),
     on the synthetic sets, with the time of the whole hull at each size.
@@ -489,6 +519,8 @@ def main():
     cpu = None if args.no_cpu else cpu_baseline(host, args.cpu_n)
     del dpts, outs
     torch.cuda.empty_cache()
+    f32soa = f32soa_bench(cch, torch, host["square"], max(args.steps, 3)) if "square" in host else None
+    torch.cuda.empty_cache()
     batched = None if args.no_batched else batched_bench(cch, torch, dev, stream, args.batched_sets)
     serving = serve_bench(cch, args.serve_requests) if args.serve_requests > 0 else None
     line = {
@@ -500,7 +532,7 @@ def main():
                    "hull_sizes": counts, "l2": "inputs larger than L2 (320 MB per set)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-        "gpu_launches": launches, "batched": batched, "serving": serving,
+        "gpu_launches": launches, "batched": batched, "serving": serving, "f32soa": f32soa,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -67,6 +67,8 @@ def _load():
         lib.cch_hull_noalloc.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
         lib.cch_hull_host.restype = ctypes.c_int
         lib.cch_hull_host.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
+        lib.cch_hull_f32soa.restype = ctypes.c_int
+        lib.cch_hull_f32soa.argtypes = [vp, vp, i64, vp, vp, vp]
         lib.cch_hull_stages.restype = ctypes.c_int
         lib.cch_hull_stages.argtypes = [vp, i64, ctypes.c_int, u32, vp, vp, vp, vp, vp, vp, vp]
         lib.cch_workspace_bytes.restype = ctypes.c_size_t
@@ -156,6 +158,38 @@ def hull(points, stream=None):
     h = int(out_count.item())
     if h < 0:
         raise CchError(h, "cch_hull (device)")
+    return out_idx[:h]
+
+
+def hull_f32soa_async(x, y, out_idx=None, out_count=None, stream=None):
+    """Enqueue the hull of the points (x[i], y[i]) given as two float32 CUDA
+    vectors (the paper's input form).  The coordinates widen exactly to
+    float64, so the result is hull_async's on torch.stack([x, y], 1).double().
+    Returns (out_idx, out_count) device tensors as hull_async does."""
+    import torch
+    for t in (x, y):
+        if not t.is_cuda or t.dtype != torch.float32 or t.dim() != 1 or not t.is_contiguous():
+            raise ValueError("x and y must be contiguous 1-D float32 CUDA tensors")
+    if x.shape[0] != y.shape[0]:
+        raise ValueError("x and y must have the same length")
+    n = x.shape[0]
+    dev = x.device
+    if out_idx is None:
+        out_idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int32, device=dev)
+    rc = _load().cch_hull_f32soa(x.data_ptr() if n else None, y.data_ptr() if n else None, n,
+                                 out_idx.data_ptr(), out_count.data_ptr(), _stream_handle(stream))
+    _check(rc, "cch_hull_f32soa")
+    return out_idx, out_count
+
+
+def hull_f32soa(x, y, stream=None):
+    """Hull vertex indices of float32 SoA points (synchronises)."""
+    out_idx, out_count = hull_f32soa_async(x, y, stream=stream)
+    h = int(out_count.item())
+    if h < 0:
+        raise CchError(h, "cch_hull_f32soa (device)")
     return out_idx[:h]
 
 

@@ -47,6 +47,13 @@ def test_status_strings_and_host_checks_without_gpu():
     assert lib.cch_hull(None, 4, 7, None, None, None) == -2
     assert lib.cch_hull(None, -1, 2, None, None, None) == -1
     assert lib.cch_workspace_bytes(-1, 2) == 0
+    lib.cch_hull_f32soa.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.cch_hull_f32soa(None, None, -1, 16, 16, None) == -1          # n < 0
+    assert lib.cch_hull_f32soa(None, 64, 4, 16, 16, None) == -1             # x missing
+    assert lib.cch_hull_f32soa(66, 64, 4, 16, 16, None) == -1               # x not 4-byte aligned
+    assert lib.cch_hull_f32soa(64, 64, 4, None, 16, None) == -1             # out_idx missing
+    assert lib.cch_hull_f32soa(64, 64, (1 << 30) + 1, 16, 16, None) == -4   # above 2^30 points
 
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")

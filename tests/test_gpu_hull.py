@@ -86,7 +86,10 @@ def test_random_sizes(kind, n):
     check(p)
 
 
-@pytest.mark.parametrize("n", [3, 1000, 4098, 70_000, 300_000])
+# 16388 / 16392 put about 4096 kept candidates in each region (the edge of
+# the shared-memory record path), 20000 about 5000 (the counting path on
+# global records), 70000 and up take the multi-block path
+@pytest.mark.parametrize("n", [3, 1000, 4098, 16_388, 16_392, 20_000, 70_000, 300_000])
 def test_all_extreme_circle(n):
     p = inputs.circle_f64(n, seed=n)
     h = check(p)
@@ -218,6 +221,63 @@ def test_device_errors_are_reported_in_the_count():
     assert int(cnt.item()) == -4
     # the context stays usable
     check(inputs.square_f64(10_000, 2))
+
+
+# ---------------------------------------- float32 SoA input (Fig. 6 form)
+
+def f32soa_hull(x, y):
+    tx = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(DEV)
+    ty = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).to(DEV)
+    return cch.hull_f32soa(tx, ty).cpu().numpy()
+
+
+def check_f32(p32):
+    """float32 points: the oracle's hull of their exact float64 values."""
+    got = f32soa_hull(p32[:, 0], p32[:, 1])
+    want = oracle.hull(p32.astype(np.float64))
+    assert np.array_equal(got, want), (p32.shape, got[:10], want[:10], len(got), len(want))
+    return got
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 4097, 100_003, 1_000_001])
+@pytest.mark.parametrize("kind", ["square", "disk", "gauss"])
+def test_f32soa_matches_oracle(kind, n):
+    seed = n % 89
+    p = {"square": lambda: inputs.square_f64(n, seed),
+         "disk": lambda: inputs.disk_f64(n, seed),
+         "gauss": lambda: inputs.gauss_f64(n, seed)}[kind]()
+    check_f32(p.astype(np.float32))
+
+
+def test_f32soa_special_values_and_unaligned_vectors():
+    """Subnormal, signed-zero, huge and duplicate float32 coordinates (the
+    widening normalises subnormals), and x / y views that start one float
+    into their buffers."""
+    rng = np.random.default_rng(23)
+    sub = rng.integers(1, 1 << 23, (3000, 2), dtype=np.uint32)
+    sub |= (rng.integers(0, 2, (3000, 2), dtype=np.uint32) << 31)
+    tiny = sub.view(np.float32)
+    big = (rng.random((3000, 2)) * 2 - 1).astype(np.float32) * np.float32(3.0e38)
+    zeros = np.array([[0.0, -0.0], [-0.0, 0.0], [0.0, 0.0], [-0.0, -0.0]], dtype=np.float32)
+    for p in (tiny, big, np.concatenate([tiny, zeros, tiny[:50]]), np.concatenate([big, tiny, zeros])):
+        check_f32(p)
+    base = inputs.disk_f64(100_001, 7).astype(np.float32)
+    bx = torch.from_numpy(np.ascontiguousarray(base[:, 0])).to(DEV)
+    by = torch.from_numpy(np.ascontiguousarray(base[:, 1])).to(DEV)
+    got = cch.hull_f32soa(bx[1:], by[1:]).cpu().numpy()
+    assert np.array_equal(got, oracle.hull(base[1:].astype(np.float64)))
+
+
+def test_f32soa_nonfinite_is_reported():
+    p = inputs.square_f64(5000, 3).astype(np.float32)
+    for bad in (np.nan, np.inf, -np.inf):
+        q = p.copy()
+        q[1234, 1] = bad
+        x = torch.from_numpy(np.ascontiguousarray(q[:, 0])).to(DEV)
+        y = torch.from_numpy(np.ascontiguousarray(q[:, 1])).to(DEV)
+        _, cnt = cch.hull_f32soa_async(x, y)
+        assert int(cnt.item()) == -3
+    assert np.array_equal(f32soa_hull(p[:, 0], p[:, 1]), oracle.hull(p.astype(np.float64)))
 
 
 def test_host_errors_return_codes():
