@@ -1,7 +1,7 @@
 """Pins for the CPU oracle (no GPU): the oracle is checked against things
 other than itself -- exact rational brute force, closed forms, invariants and
 the worked example of Fig. 4 -- so that a dropped term, a flipped sign or a
-swapped operand in it fails here before it is trusted as the GPU's judge."""
+swapped operand in it fails here before the GPU path is compared with it."""
 import os
 from fractions import Fraction
 
