@@ -47,6 +47,12 @@ struct PointT<DT_I32> { using T = int2; };
 
 // ------------------------------------------------------------- keys
 
+// Top word of the smallest magnitude the float64 domain takes, 2^-400, read
+// as FP32 (0x26F00000): a coordinate whose top word reads below it in
+// magnitude is zero or possibly too small, and gets the exact test.
+constexpr uint32_t kTinyTopBits = (1023u - 400u) << 20;
+#define kTinyTopF __uint_as_float(kTinyTopBits)
+
 // Order-preserving key of a float64 as 32-bit words (-0.0 -> +0.0).  Also
 // folds the magnitude of a nonzero value into `amin` (top word), for the
 // lower end of the domain check.
@@ -161,6 +167,26 @@ __device__ __forceinline__ void a1_update(uint32_t xh, uint32_t xl, uint32_t yh,
 __device__ __forceinline__ void a1_thresholds(const Lex best[4], uint32_t th[4]) {
 #pragma unroll
   for (int e = 0; e < 4; e++) th[e] = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(best[e].k1 >> 32));
+}
+
+// float64 filter on the top 32 bits of each coordinate read as an FP32
+// number.  Over the domain (|c| < 2^400, or zero) that reading is monotone in
+// the coordinate, -0.0 and +0.0 compare equal, and every coordinate outside
+// it (huge, Inf, NaN) reads as a NaN, which the unordered tests below let
+// through to the exact update (where it becomes an extreme and setup_set
+// reports it).  A threshold is the top word of the warp's running bound
+// turned back from key to bits: a point passes when its top word is at or
+// beyond the bound's, so the exact keys still decide every tie.
+__device__ __forceinline__ float a1_bound_f(uint32_t keyhi) {
+  const uint32_t raw = (keyhi & 0x80000000u) ? (keyhi ^ 0x80000000u) : ~keyhi;
+  return __uint_as_float(raw);
+}
+__device__ __forceinline__ void a1_thresholds_f(const Lex best[4], float thf[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const uint32_t t = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(best[e].k1 >> 32));
+    thf[e] = a1_bound_f(e >= 2 ? ~t : t);
+  }
 }
 
 // Bucket of the stairs map: monotone non-decreasing in u.
@@ -409,8 +435,10 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   // ------------------------------------------------------------ consumers
   Lex best[4];
   uint32_t th[4];
+  float thf[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; th[k] = 0xFFFFFFFFu; }
+  a1_thresholds_f(best, thf);
   uint32_t amin = 0x7FFFFFFFu;
   // set-local indices fit in 32 bits (n <= 2^30)
   for (int it = 0; it < ntile; it++) {
@@ -427,6 +455,56 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     const int np = (int)min((int64_t)TILE, sd.n - t0);
     const unsigned char* base = smem + slot * SB + 16 - st_head[slot] * PB;
     const int wb = warp * WPTS;
+    if constexpr (DT == DT_F64) {
+      // raw words; the filter and the small-magnitude test in FP32 on the
+      // top words, the exact key work only where they fire
+      uint32_t xh[IW], xl[IW], yh[IW], yl[IW];
+      uint32_t passm = 0, tinym = 0;
+#pragma unroll
+      for (int k = 0; k < IW; k++) {
+        const int i = wb + k * 32 + lane;
+        if (i < np) {
+          const uint4 q = *reinterpret_cast<const uint4*>(base + i * PB);
+          xl[k] = q.x; xh[k] = q.y; yl[k] = q.z; yh[k] = q.w;
+          const float fx = __uint_as_float(q.y), fy = __uint_as_float(q.w);
+          const bool pass = !(fx > thf[0]) | !(fy > thf[1]) | !(fx < thf[2]) | !(fy < thf[3]);
+          const bool tiny = (fabsf(fx) < kTinyTopF) | (fabsf(fy) < kTinyTopF);
+          passm |= (uint32_t)pass << k;
+          tinym |= (uint32_t)tiny << k;
+        } else {
+          xh[k] = yh[k] = xl[k] = yl[k] = 0u;
+        }
+      }
+      __syncwarp();
+      if (lane == 0)   // the warp is done with the stage: release it to the producer
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
+      // rare: zeros and tiny magnitudes (the exact lower end of the domain check)
+      if (__any_sync(0xFFFFFFFFu, tinym != 0)) {
+#pragma unroll
+        for (int k = 0; k < IW; k++) {
+          if ((tinym >> k) & 1u) {
+            uint32_t a = xh[k] & 0x7FFFFFFFu;
+            if ((a | xl[k]) != 0) amin = min(amin, a);
+            a = yh[k] & 0x7FFFFFFFu;
+            if ((a | yl[k]) != 0) amin = min(amin, a);
+          }
+        }
+      }
+      // rare: a warp-uniform branch keeps the full update out of the hot path
+      if (__any_sync(0xFFFFFFFFu, passm != 0)) {
+#pragma unroll
+        for (int k = 0; k < IW; k++) {
+          if ((passm >> k) & 1u) {
+            uint32_t kxh, kxl, kyh, kyl, dummy = 0;
+            f64_key_words(((uint64_t)xh[k] << 32) | xl[k], kxh, kxl, dummy);
+            f64_key_words(((uint64_t)yh[k] << 32) | yl[k], kyh, kyl, dummy);
+            a1_update<DT>(kxh, kxl, kyh, kyl, i0 + wb + k * 32 + lane, best);
+          }
+        }
+        a1_thresholds_f(best, thf);
+      }
+      continue;
+    }
     uint32_t xh[IW], xl[IW], yh[IW], yl[IW];
     bool need = false;
 #pragma unroll
