@@ -14,6 +14,10 @@ Contents
   * ``orient(a, b, c)``   -- the exact orientation predicate used by both.
   * ``bruteforce``        -- O(n^3) hull and O(n^2) SPA by exact rationals, the
     pins for the C code.
+  * ``parallel_hull(points)`` -- the multi-core CPU baseline the benchmark
+    times beside the oracle (OpenMP: octagon filter, parallel merge sort,
+    Andrew's chain; ``cch_cpu_parallel.c`` includes the oracle's source for
+    its exact predicates); the tests check it returns exactly ``hull``.
 
 Parity status: every function here is pinned by tests in ``tests/test_oracle*.py``
 against brute force on exact rationals, closed forms and invariants, except
@@ -32,8 +36,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cch_oracle.c")
 _LIB = os.path.join(_HERE, "libcchoracle.so")
+_PSRC = os.path.join(_HERE, "cch_cpu_parallel.c")
+_PLIB = os.path.join(_HERE, "libcchpar.so")
 _lock = threading.Lock()
 _lib = None
+_plib = None
 
 I32 = 1
 F64 = 2
@@ -51,6 +58,64 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_parallel(force: bool = False):
+    """Compile the multi-core CPU baseline (OpenMP; it includes the oracle's
+    source).  Returns the library path, or None where gcc has no OpenMP."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_PSRC))
+    if not force and os.path.exists(_PLIB) and os.path.getmtime(_PLIB) >= newest:
+        return _PLIB
+    tmp = _PLIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _PSRC, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=_HERE)
+    if r.returncode != 0:
+        return None
+    os.replace(tmp, _PLIB)
+    return _PLIB
+
+
+def _load_parallel():
+    global _plib
+    with _lock:
+        if _plib is None:
+            path = build_parallel()
+            if path is None:
+                return None
+            lib = ctypes.CDLL(path)
+            vp, i64 = ctypes.c_void_p, ctypes.c_int64
+            lib.cpu_parallel_hull_i32.restype = i64
+            lib.cpu_parallel_hull_i32.argtypes = [vp, i64, vp, ctypes.c_int]
+            lib.cpu_parallel_hull_f64.restype = i64
+            lib.cpu_parallel_hull_f64.argtypes = [vp, i64, vp, ctypes.c_int]
+            lib.cpu_parallel_threads.restype = ctypes.c_int
+            lib.cpu_parallel_threads.argtypes = []
+            _plib = lib
+    return _plib
+
+
+def parallel_available() -> bool:
+    return _load_parallel() is not None
+
+
+def parallel_threads() -> int:
+    return _load_parallel().cpu_parallel_threads()
+
+
+def parallel_hull(points, threads: int = 0) -> np.ndarray:
+    """The multi-core CPU baseline (quadrilateral filter, parallel merge
+    sort, Andrew's chain on the oracle's predicates): the same indices as
+    hull().  threads = 0 uses every core OpenMP offers."""
+    p, dt = _prep(points)
+    n = p.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    lib = _load_parallel()
+    if lib is None:
+        raise RuntimeError("the parallel CPU baseline needs gcc with OpenMP")
+    fn = lib.cpu_parallel_hull_i32 if dt == I32 else lib.cpu_parallel_hull_f64
+    h = fn(p.ctypes.data, n, out.ctypes.data, int(threads))
+    return out[:h].copy()
 
 
 def _load():

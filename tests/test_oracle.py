@@ -278,3 +278,23 @@ def test_blocked_spa_of_the_paper_is_a_superset():
                     t = pl[i][c]
                     blocked.add(i)
         assert set(m["spa"][k].tolist()) <= blocked
+
+
+# ------------------------------------------------ multi-core CPU baseline
+
+@pytest.mark.skipif(not oracle.parallel_available(), reason="gcc without OpenMP")
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_parallel_baseline_equals_oracle(threads):
+    """The benchmark's multi-core CPU baseline (octagon filter, parallel merge
+    sort, Andrew's chain) returns exactly the oracle's hull."""
+    rng = np.random.default_rng(31)
+    t = rng.random(3000)
+    cases = [inputs.square_f64(60_000, 1), inputs.disk_f64(70_001, 2), inputs.gauss_f64(50_000, 3),
+             inputs.square_i32(40_000, 4), inputs.degenerate_f64(50_000, 9), inputs.circle_f64(5_000, 6),
+             np.zeros((0, 2)), np.ones((5, 2)), np.array([[1.0, 2.0]]), np.array([[1.0, 2.0], [1.0, 2.0]]),
+             np.array([[0.0, 0.0], [1.0, 1.0], [2.0, 2.0], [0.5, 0.5]]),
+             rng.integers(0, 3, (1000, 2)).astype(np.int32), rng.integers(-5, 5, (5000, 2)).astype(np.float64),
+             np.array([[0, 0], [2, 0], [2, 2], [0, 2], [1, 1], [0, 0], [2, 2]], dtype=np.int32),
+             np.stack([t, 0.5 * t + 1e-17 * rng.standard_normal(3000)], 1)]
+    for p in cases:
+        assert np.array_equal(oracle.parallel_hull(p, threads), oracle.hull(p)), p.shape
