@@ -170,11 +170,12 @@ __device__ __forceinline__ void a1_thresholds(const Lex best[4], uint32_t th[4])
 }
 
 // float64 filter on the top 32 bits of each coordinate read as an FP32
-// number.  Over the domain (|c| < 2^400, or zero) that reading is monotone in
-// the coordinate, -0.0 and +0.0 compare equal, and every coordinate outside
-// it (huge, Inf, NaN) reads as a NaN, which the unordered tests below let
-// through to the exact update (where it becomes an extreme and setup_set
-// reports it).  A threshold is the top word of the warp's running bound
+// number.  That reading is non-decreasing in the coordinate wherever it is
+// not NaN and -0.0 and +0.0 compare equal; the largest magnitudes (from
+// 2^1017 on) and Inf / NaN inputs read as +-Inf, ordered beyond every other
+// reading, or as NaN, which the unordered tests below let through -- either
+// way such a value reaches the exact update, becomes an extreme, and
+// setup_set reports it.  A threshold is the top word of the warp's running bound
 // turned back from key to bits: a point passes when its top word is at or
 // beyond the bound's, so the exact keys still decide every tie.
 __device__ __forceinline__ float a1_bound_f(uint32_t keyhi) {

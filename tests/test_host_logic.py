@@ -1,0 +1,121 @@
+"""CPU checks of the numeric facts the kernels rely on (no GPU).
+
+These restate, in numpy, two bit-level maps the CUDA code uses and check
+them against IEEE 754 arithmetic, so that the reasoning behind the kernels is
+pinned independently of the kernels themselves (which the GPU tests check
+end to end against the oracle):
+
+* a1's float64 filter reads the top 32 bits of a coordinate as an FP32
+  number: that reading must be non-decreasing in the coordinate wherever it
+  is not NaN (+-Inf included), equal for -0.0 and +0.0, and NaN or +-Inf only
+  for values the domain check rejects at the top (|c| >= 2^1017, Inf, NaN);
+  the warp's integer key bound maps back to those bits exactly;
+* cch_hull_f32soa widens float32 to float64 from the IEEE bit fields.
+"""
+import numpy as np
+
+
+def top_reading(d):
+    """The top 32 bits of float64 values read as float32."""
+    bits = np.asarray(d, dtype=np.float64).view(np.uint64)
+    return (bits >> np.uint64(32)).astype(np.uint32).view(np.float32)
+
+
+def key_hi(d):
+    """Order-preserving key of the top word (-0.0 made +0.0), as a1 builds it."""
+    bits = np.asarray(d, dtype=np.float64).view(np.uint64)
+    h = (bits >> np.uint64(32)).astype(np.uint32)
+    lo = (bits & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    nz = ((h & np.uint32(0x7FFFFFFF)) | lo) != 0
+    h = np.where(nz, h, np.uint32(0))
+    m = np.where(h >> np.uint32(31) == 1, np.uint32(0xFFFFFFFF), np.uint32(0))
+    return h ^ (m | np.uint32(0x80000000))
+
+
+def bound_bits(k):
+    """a1_bound_f: a key's top word back to raw bits."""
+    k = np.asarray(k, dtype=np.uint32)
+    return np.where(k & np.uint32(0x80000000) != 0, k ^ np.uint32(0x80000000), ~k)
+
+
+def sample_doubles(rng, n):
+    e = rng.integers(-1074, 1024, n).astype(np.float64)
+    v = rng.random(n) * np.exp2(e)
+    v *= np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.0 ** -400, -(2.0 ** -400), 2.0 ** 400, 2.0 ** 1016,
+                        2.0 ** 1017, -(2.0 ** 1017), np.finfo(np.float64).max, np.inf, -np.inf, 1.0, -1.0])
+    return np.concatenate([v, special])
+
+
+def test_top_word_reading_is_monotone_and_non_finite_only_out_of_domain():
+    rng = np.random.default_rng(41)
+    d = sample_doubles(rng, 200_000)
+    d = d[~np.isnan(d)]
+    d = np.sort(d)
+    t = top_reading(d)
+    biased = (d.view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF)
+    out = biased >= 2040                             # |c| >= 2^1017, Inf
+    assert np.array_equal(~np.isfinite(t), out)      # NaN or +-Inf exactly there
+    assert not np.isnan(t[~out]).any()
+    ok = ~np.isnan(t)
+    tt = t[ok]
+    assert np.all(tt[1:] >= tt[:-1])                 # non-decreasing in the coordinate
+    assert top_reading(-0.0) == top_reading(0.0)
+    # the largest in-domain magnitude reads below every out-of-domain one
+    assert top_reading(np.nextafter(2.0 ** 400, 0)) < top_reading(2.0 ** 1017)
+
+
+def test_key_bound_maps_back_to_the_top_bits():
+    rng = np.random.default_rng(43)
+    d = sample_doubles(rng, 100_000)
+    d = d[~np.isnan(d) & (d != 0)]                   # -0.0 is normalised by the key, checked below
+    k = key_hi(d)
+    raw = (d.view(np.uint64) >> np.uint64(32)).astype(np.uint32)
+    assert np.array_equal(bound_bits(k), raw)
+    # the complemented (maximum) bound: the kernel stores ~key and maps ~(~key)
+    assert np.array_equal(bound_bits(~(~k)), raw)
+    # -0.0 and +0.0 share a key; its bits read as +0.0, which compares equal to -0.0
+    assert key_hi(-0.0) == key_hi(0.0)
+    assert bound_bits(key_hi(-0.0)).view(np.float32) == np.float32(0.0)
+    # ordering: key order equals value order, so a point whose top word reads at
+    # or below the bound's reading has key <= the bound's key or ties it
+    a, b = np.sort(rng.choice(d, 2, replace=False))
+    assert key_hi(a) <= key_hi(b)
+
+
+def test_the_no_extreme_bound_lets_everything_through():
+    # no extreme yet: the running minimum key is all ones, its bits read as NaN
+    assert np.isnan(bound_bits(np.uint32(0xFFFFFFFF)).view(np.float32))
+    assert np.isnan(bound_bits(~np.uint32(0xFFFFFFFF)).view(np.float32))
+
+
+def widen(u):
+    """cch_hull_f32soa's widening, from the float32 bit fields."""
+    sign = (u >> 31) << 63
+    e = (u >> 23) & 0xFF
+    m = u & 0x7FFFFF
+    if e == 0xFF:
+        return sign | (0x7FF << 52) | (m << 29)
+    if e != 0:
+        return sign | ((e + 896) << 52) | (m << 29)
+    if m == 0:
+        return sign
+    p = m.bit_length() - 1
+    return sign | ((p + 874) << 52) | ((m << (52 - p)) & ((1 << 52) - 1))
+
+
+def test_widening_matches_ieee_conversion():
+    rng = np.random.default_rng(47)
+    u = np.concatenate([rng.integers(0, 2 ** 32, 50_000, dtype=np.uint64).astype(np.uint32),
+                        np.arange(0, 3000, dtype=np.uint32), np.arange(0x80000000, 0x80000800, dtype=np.uint32),
+                        np.array([0x7F800000, 0xFF800000, 0x007FFFFF, 0x00800000, 0x807FFFFF, 0x7F7FFFFF,
+                                  0x7FC00000, 0xFFC00001], dtype=np.uint32)])
+    f = u.view(np.float32)
+    with np.errstate(invalid="ignore"):
+        ref = f.astype(np.float64)
+    for x, r in zip(u.tolist(), ref.tolist()):
+        w = np.uint64(widen(x)).view(np.float64)
+        if np.isnan(r):
+            assert np.isnan(w)
+        else:
+            assert w == r and np.signbit(w) == np.signbit(r), hex(x)
