@@ -118,6 +118,22 @@ def gen_inputs(n, kinds=KINDS):
     return {k: inputs.headline_f64(k, n) for k in kinds}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of `x` over the ranks (the slowest rank bounds a
+    step); `dist` is torch.distributed, or None for one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_all_ranks, ms_step):
+    """Mpoints/s of the whole job: every rank's points over the slowest rank's step time."""
+    return points_all_ranks / (ms_step * 1e-3) / 1e6
+
+
 def cpu_baseline(pts, sample_n):
     """The C oracle (single thread, as it stands) on the first `sample_n` points of each set;
     beside it (key `parallel`) the multi-core CPU baseline on the same sample and every core
@@ -480,14 +496,10 @@ def main():
     launches = cch.launch_count() - l0
     stage_ms, calls = cch.profile_read()
     cch.profile(False)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_step = ms / args.steps
     pts_step = len(kinds) * args.n * world
-    value = pts_step / (ms_step * 1e-3) / 1e6
+    value = whole_job_rate(pts_step, ms_step)
 
     # roofline of the dominant streaming kernel (one read of the points per launch)
     hbm, hbm_src = peaks()
@@ -537,11 +549,7 @@ def main():
     for _ in range(e2e_steps):
         d2h = e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
     pool.shutdown()
     e2e = {"value": pts_step / e2e_s / 1e6, "unit": "Mpoints/s", "h2d_bytes_per_step": len(kinds) * 16 * args.n,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
