@@ -137,8 +137,11 @@ int cch_hull_f32soa(const float *x, const float *y, int64_t n, int32_t *out_idx,
  *   r1_region     device int32[max(n,1)]: their regions 1..4
  *   spa_idx       device int32[max(n,1)]: SPA survivors (Fig. 2) of R1..R4
  *                 in sorted (Table 1) order, region after region
- *   counts_host   host int64[10]: s1, records of R1..R4, survivors of R1..R4,
- *                 and the device status (0 or a negative code)
+ *   counts_host   host int64[11]: s1, records of R1..R4, survivors of R1..R4,
+ *                 the device status (0 or a negative code), and the number of
+ *                 LSD radix passes the multi-block sort ran (0 when the set
+ *                 took the shared-memory path; byte passes whose digit is the
+ *                 same for every record are skipped)
  *   out_idx, out_count   as for cch_hull
  * Synchronises the stream before returning.
  */

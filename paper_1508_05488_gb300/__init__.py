@@ -262,7 +262,8 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None
 
     ``r1`` list of 4 int32 arrays (round-1 survivors per region, index order),
     ``spa`` list of 4 int32 arrays (SPA survivors per region, sorted order),
-    ``hull`` int32 array, ``counts`` int64[10], ``status``."""
+    ``hull`` int32 array, ``counts`` int64[11], ``status``, ``passes`` (radix
+    passes of the multi-block sort, 0 on the shared-memory path)."""
     import torch
     _check_points(points)
     n = points.shape[0]
@@ -273,7 +274,7 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None
     spa = torch.empty(m, dtype=torch.int32, device=dev)
     out_idx = torch.empty(m, dtype=torch.int32, device=dev)
     out_count = torch.empty(1, dtype=torch.int32, device=dev)
-    counts = np.zeros(10, dtype=np.int64)
+    counts = np.zeros(11, dtype=np.int64)
     rc = _load().cch_hull_stages(points.data_ptr() if n else None, n, _dtype_code(points),
                                  (1 if exact_only else 0) | (0 if prefilter else 2),
                                  r1.data_ptr(), r1r.data_ptr(),
@@ -298,6 +299,7 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None
         "count": h,
         "counts": counts,
         "status": int(counts[9]),
+        "passes": int(counts[10]),
     }
 
 

@@ -330,6 +330,9 @@ __global__ void __launch_bounds__(kThreads) k_widen(const float* __restrict__ x,
 }
 
 }  // namespace
+
+void count_launches(uint64_t n) { g_launches += n; }
+
 }  // namespace cch
 
 using namespace cch;
@@ -508,6 +511,7 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   for (int r = 0; r < 4; r++) counts_host[1 + r] = c.cnt[r];
   for (int r = 0; r < 4; r++) counts_host[5 + r] = c.s2[r];
   counts_host[9] = c.status != 0 ? c.status : (int32_t)ctr[CT_ERR];
+  counts_host[10] = c.passes;
   return CCH_OK;
 }
 

@@ -4,16 +4,21 @@
 // Pipeline (Sec. 2.1, steps 1-7), every stage a kernel, every set of points a
 // "set" (a single hull is a batch of one):
 //   a1  k_extremes      four lexicographic extremes + edge set-up (step 1)
-//   a2  k_classify      quadrilateral test, region routing, stable compaction
-//                       of the survivors into one record stream (steps 2-3)
-//   a3  k_sort_hist +   LSD radix sort of the records by the Table 1 key,
-//       k_sort_pass     then by region (step 4)
-//   a4  k_spa           SPA as a segmented exclusive prefix-minimum scan with
-//                       stable compaction into per-region chains (step 5)
+//       k_stairs        dominance tables and box from a sample of each set
+//   a2  k_classify      quadrilateral test, region routing and dominance
+//                       prefilter; survivors compacted in place per tile
+//                       (steps 2-3)
+//       k_gather        survivors moved into region-major order; per set the
+//                       choice between the two sort paths
+//   a3+ k_small         per (set, region) in one CTA: Table 1 sort and Fig. 2
+//   a4                  SPA in shared memory (steps 4-5)
+//       k_big           sets with a region above kSmallMax records: LSD radix
+//                       sort and SPA as a segmented prefix-minimum scan, one
+//                       cooperative persistent kernel (steps 4-5)
 //   a5  k_chain_local + strictly convex chain per region (steps 6-7; the
 //       k_chain_merge + paper's CPU Melkman stage is replaced by chunked
-//       k_output        monotone-chain hulls merged by bridge walks) and the
-//                       output compaction
+//       k_output        hulls merged by bridge walks) and the output
+//                       compaction
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -69,7 +74,6 @@ constexpr int kSortPasses = 9;         // 8 key bytes + the region digit
 // A set whose four regions each hold at most kSmallMax round-1 survivors is
 // sorted and SPA-scanned by one CTA per region in shared memory.
 constexpr int kSmallMax = 16384;
-constexpr int kSmallThreads = 1024;
 constexpr int kSpaItems = 8;
 constexpr int kSpaTile = kThreads * kSpaItems;      // 2048 records
 constexpr int kChainItems = 16;
@@ -174,7 +178,7 @@ struct SetCtl {
   float    slo[4], shi[4], sscale[4];  // stairs bucket map of region r: b = (u - lo) * scale
   float    bx0, bx1, by0, by1;          // dominance box (FP32 views, open; empty when zero)
   uint32_t arrive3;          // stairs chunk arrivals
-  uint32_t pad1;
+  uint32_t passes;           // radix passes the multi-block sort ran for this set
 };
 
 // SPA prefix-minimum look-back status of one tile: value words published
@@ -784,6 +788,7 @@ int launch_chain(const Job& j, const Ws& w, const Launch& L);
 // stage extraction (cch_hull_stages)
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
 int extremes_blocks_per_sm(int dtype);
+void count_launches(uint64_t n);   // add to the library's launch counter (cch_launch_count)
 void serve_release_pinned();   // free the server's pooled pinned host buffers
 
 }  // namespace cch

@@ -257,6 +257,7 @@ __device__ void big_pass(const Job& j, const Ws& w, int p, uint32_t total) {
       else skip = full;
     }
     if (skip) continue;   // uniform across the CTA
+    if (lt == 0 && threadIdx.x == 0) w.ctl[s].passes++;   // one CTA per (pass, set); passes are barrier-separated
     const uint64_t* kin = par ? w.keyB : w.keyA;
     const uint32_t* vin = par ? w.valB : w.valA;
     uint64_t* kout = par ? w.keyA : w.keyB;

@@ -16,8 +16,12 @@
 //   * at most kNoAllocMaxPoints points (sets of any larger size are rejected
 //     with CCH_ERR_RANGE before anything is launched);
 //   * every call on a device shares the one array and the array keeps the
-//     last call's contents: the per-call control words are cleared by each
-//     call, the look-back words once per 4095 calls;
+//     last call's contents.  The array has one fixed layout, sized for the
+//     largest call, so every buffer sits at the same place in every call.
+//     The per-call control words are cleared by each call.  Look-back words
+//     carry the call's epoch (1..4095) and read as "not ready" in any other
+//     call; when the epoch wraps, the whole look-back region is cleared, so
+//     no word of an earlier cycle can be taken for one of this call;
 //   * calls whose work overlaps on the GPU (different streams, no ordering
 //     between them) race on the shared array and give wrong results: order
 //     them (one stream, or events);
@@ -45,14 +49,21 @@ int g_na_sms[kMaxDevices] = {};
 
 size_t na_up(size_t v) { return (v + 255) / 256 * 256; }
 
-// Carve the workspace of a one-set call of up to `n` points out of `base`
-// (sizes only when base is null).  Returns the bytes used; `ctl_bytes` is the
-// per-call cleared prefix, [status_off, status_off + status_bytes) the
-// look-back words.
-size_t na_layout(int64_t n, int32_t nchunk1, int32_t ntile2, char* base, Ws& w, size_t& ctl_bytes,
-                 size_t& status_off, size_t& status_bytes) {
+// Largest a1 chunk count and a2 tile count of any call: a1 chunks hold at
+// least 4096 points, a2 tiles at least cls_tile(CCH_F64) = 2048.
+constexpr int32_t kNaMaxChunk1 = (int32_t)((kNoAllocMaxPoints + 4095) / 4096);
+constexpr int32_t kNaMaxTile2 = (int32_t)((kNoAllocMaxPoints + 2047) / 2048);
+
+// The one fixed layout of the array, sized for kNoAllocMaxPoints points and
+// the largest chunk and tile counts, so that every buffer -- in particular
+// the look-back words -- sits at the same address in every call, whatever its
+// size or dtype (a call of fewer points uses a prefix of each buffer).
+// Returns the bytes used; [0, ctl_bytes) is cleared by every call,
+// [status_off, status_off + status_bytes) holds every look-back word.
+size_t na_layout(char* base, Ws& w, size_t& ctl_bytes, size_t& status_off, size_t& status_bytes) {
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = na_up(o + bytes); return base ? base + r : nullptr; };
+  const int64_t n = kNoAllocMaxPoints;
   const int64_t nc = n + 8;
   const int64_t sort_tiles = n / kSortTile + 2;
   const int64_t spa_tiles = n / kSpaTile + 5;
@@ -61,7 +72,7 @@ size_t na_layout(int64_t n, int32_t nchunk1, int32_t ntile2, char* base, Ws& w, 
   w = Ws{};
   w.ctl = (SetCtl*)take(sizeof(SetCtl));
   w.ctr = (uint32_t*)take(sizeof(uint32_t) * CT_COUNT);
-  w.ptot = (uint4*)take(16 * ((size_t)ntile2 / kPlanTiles + 2));
+  w.ptot = (uint4*)take(16 * ((size_t)kNaMaxTile2 / kPlanTiles + 2));
   ctl_bytes = o;
   status_off = o;
   w.st_sort = (uint64_t*)take(8 * 256 * (size_t)sort_tiles);
@@ -69,8 +80,8 @@ size_t na_layout(int64_t n, int32_t nchunk1, int32_t ntile2, char* base, Ws& w, 
   w.st_spa_cnt = (uint64_t*)take(8 * (size_t)spa_tiles);
   w.st_out = (uint64_t*)take(8 * (size_t)out_tiles);
   status_bytes = o - status_off;
-  w.part = (Part*)take(sizeof(Part) * (size_t)(nchunk1 > 0 ? nchunk1 : 1));
-  w.tcnt = (uint64_t*)take(8 * 8 * (size_t)(ntile2 > 0 ? ntile2 : 1));
+  w.part = (Part*)take(sizeof(Part) * (size_t)kNaMaxChunk1);
+  w.tcnt = (uint64_t*)take(8 * 8 * (size_t)kNaMaxTile2);
   w.small_seg = (uint32_t*)take(16);
   w.keyA = (uint64_t*)take(8 * (size_t)n);
   w.keyB = (uint64_t*)take(8 * (size_t)n);
@@ -148,7 +159,7 @@ extern "C" int cch_hull_noalloc(const void* points, int64_t n, int dtype, int32_
   }
   Ws w;
   size_t ctl_bytes = 0, status_off = 0, status_bytes = 0;
-  const size_t need = na_layout(n, j.nchunk1, j.ntile2, g_na_ptr[dev], w, ctl_bytes, status_off, status_bytes);
+  const size_t need = na_layout(g_na_ptr[dev], w, ctl_bytes, status_off, status_bytes);
   if (need > kNoAllocBytes) return CCH_ERR_RANGE;
 
   if (++g_na_epoch[dev] > 0xFFFu) {
@@ -159,13 +170,15 @@ extern "C" int cch_hull_noalloc(const void* points, int64_t n, int dtype, int32_
   if (cudaMemsetAsync(g_na_ptr[dev], 0, ctl_bytes, st) != cudaSuccess) return CCH_ERR_CUDA;
 
   Launch L{st, sms * 4, 2 * sms};
-  launch_extremes(j, w, L);
-  launch_stairs(j, w, L);
-  launch_classify(j, w, L);
-  launch_gather(j, w, L);
-  launch_small(j, w, L);
-  launch_big(j, w, L);
-  launch_chain(j, w, L);
+  int nk = 0;
+  nk += launch_extremes(j, w, L);
+  nk += launch_stairs(j, w, L);
+  nk += launch_classify(j, w, L);
+  nk += launch_gather(j, w, L);
+  nk += launch_small(j, w, L);
+  nk += launch_big(j, w, L);
+  nk += launch_chain(j, w, L);
+  count_launches((uint64_t)nk);
   if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
   return CCH_OK;
 }
