@@ -271,54 +271,141 @@ def batched_bench(cch, torch, dev, stream, nsets):
             "speedup_vs_per_call": ms_calls / ms_batch, "identical_to_per_call": same}
 
 
-def serve_bench(cch, requests_per_load, pool_size=16):
-    """Poisson stream of float64 hull requests (sizes log-uniform in [1e3, 2e7],
-    square / disk / Gaussian / shell, seed 8) through the server: first the
-    closed-loop saturated rate, then offered loads of 0.5, 0.8 and 0.95 of it.
-    Every result is compared with the hull of the request computed alone."""
+def serve_bench(cch, torch, dev, requests_per_load, window=256):
+    """Poisson stream of float64 hull requests (sizes log-uniform in [1e3,
+    2e7], square / disk / Gaussian / shell, seed 8): `requests_per_load`
+    distinct requests, drawn in device memory and submitted from there
+    (cch_serve_submit_device: the request state stays device-resident).
+    First the saturated rate (closed loop, at most `window` requests
+    outstanding), then offered loads of 0.5, 0.8 and 0.95 of it.  Every
+    result is compared with the hull of the same request computed alone
+    (cch_hull).  `hulls_per_s` counts every request over first submit ->
+    last result; `drain_ms` is last result - last arrival."""
     import numpy as np
     from paper_1508_05488_gb300 import inputs
-    pool = [inputs.serve_request(i) for i in range(pool_size)]
-    alone = []
-    with cch.Server(np.float64) as srv:
-        for p in pool:
-            srv.submit(p)
-            got = []
-            while not got:
-                got = srv.poll()
-            alone.append(got[0][2])
+    reqs, alone = [], []
+    for i in range(requests_per_load):
+        d = inputs.serve_request_device(i, dev)
+        reqs.append(d)
+        alone.append(cch.hull(d).cpu().numpy())
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
 
     def run(rate):
         arrivals = inputs.poisson_arrivals(requests_per_load, rate) if rate else None
-        res, ok = {}, True
+        res, which = {}, {}
         with cch.Server(np.float64) as srv:
             t0 = time.perf_counter()
-            which = {}
+            t_arr = t0
             for i in range(requests_per_load):
                 if arrivals is not None:
                     wait = t0 + arrivals[i] - time.perf_counter()
                     if wait > 0:
                         time.sleep(wait)
-                which[srv.submit(pool[i % pool_size])] = i % pool_size
+                else:
+                    while i - len(res) >= window:           # closed loop: bounded outstanding work
+                        for t, st, h, lat in srv.poll():
+                            res[t] = (st, h)
+                t_arr = time.perf_counter()
+                which[srv.submit(reqs[i], stream=stream)] = i
                 for t, st, h, lat in srv.poll():
                     res[t] = (st, h)
             while len(res) < requests_per_load:
                 for t, st, h, lat in srv.poll():
                     res[t] = (st, h)
-                time.sleep(0.0002)
-            elapsed = time.perf_counter() - t0
+                time.sleep(0.0001)
+            t_end = time.perf_counter()
             stats = srv.stats()
-        for t, (st, h) in res.items():
-            ok &= st == 0 and np.array_equal(h, alone[which[t]])
-        return {"offered_hulls_per_s": rate, "hulls_per_s": requests_per_load / elapsed,
-                "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "identical_to_alone": bool(ok)}
+        ok = all(st == 0 and np.array_equal(h, alone[which[t]]) for t, (st, h) in res.items())
+        return {"offered_hulls_per_s": rate, "hulls_per_s": requests_per_load / (t_end - t0),
+                "arrival_window_s": t_arr - t0, "drain_ms": (t_end - t_arr) * 1e3,
+                "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "samples": len(res),
+                "identical_to_alone": bool(ok)}
 
     sat = run(None)
     loads = [run(f * sat["hulls_per_s"]) for f in (0.5, 0.8, 0.95)]
-    return {"config": f"{requests_per_load} float64 requests per load drawn from {pool_size} request sets "
-                      "(sizes log-uniform in [1e3, 2e7], square/disk/Gaussian/shell, seed 8); budget 64 GiB",
-            "mean_points_per_request": float(np.mean([len(p) for p in pool])),
+    sizes = [int(r.shape[0]) for r in reqs]
+    del reqs
+    torch.cuda.empty_cache()
+    return {"config": f"{requests_per_load} distinct float64 requests per load (sizes log-uniform in [1e3, 2e7], "
+                      "square/disk/Gaussian/shell, seed 8), drawn and submitted in device memory; budget 64 GiB; "
+                      f"saturated rate in a closed loop of at most {window} outstanding requests",
+            "mean_points_per_request": float(np.mean(sizes)), "total_points": int(np.sum(sizes)),
             "saturated": sat, "loads": loads}
+
+
+# The other single-hull configurations: timed beside the headline step (not
+# part of `value`).  name: (generator, n, dtype, description)
+EXTRA_CONFIGS = (
+    ("degenerate_20M", "degenerate_f64", 20_000_000, "f64",
+     "20M float64: 4M points on the unit circle and 16M in the disk of radius 1-2^-10, all on the 2^-20 grid, "
+     "1% exact duplicates, shuffled (seed 5)"),
+    ("circle_2M", "circle_f64", 2_000_000, "f64",
+     "2M float64 points at angles 2 pi k / n on the unit circle, shuffled (seed 6): every point is a hull vertex"),
+    ("int32_1M", "square_i32", 1_000_000, "i32", "1M int32 points uniform in [0, 2^29)^2 (seed 1)"),
+)
+
+
+def extra_configs_bench(cch, torch, dev, reps, hbm):
+    """Mpoints/s, stage times and survivor counts of the degenerate, all-extreme
+    and int32 configurations; for the multi-block sort (k_big) a roofline over
+    the record bytes it moves: one read of the records for the histograms, one
+    read and one write per radix pass actually run (passes whose digit is the
+    same for every record are skipped), the SPA phase's read of every record's
+    index and point and write of the survivors' chain slots."""
+    from paper_1508_05488_gb300 import inputs
+    out = {}
+    for name, gen, n, dt, desc in EXTRA_CONFIGS:
+        host = getattr(inputs, gen)(n, {"degenerate_f64": 5, "circle_f64": 6, "square_i32": 1}[gen])
+        pts = torch.from_numpy(host).to(dev)
+        del host
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            cch.hull_async(pts, idx, cnt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            cch.hull_async(pts, idx, cnt)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        h = int(cnt.item())
+        cch.profile(True)
+        cch.profile_read()
+        for _ in range(3):
+            cch.hull_async(pts, idx, cnt)
+        st_ms, calls = cch.profile_read()
+        cch.profile(False)
+        st_ms = {k: v / max(calls, 1) for k, v in st_ms.items()}
+        ours = cch.stages(pts, prefilter=True)
+        paper = cch.stages(pts, prefilter=False)
+        s1 = int(ours["counts"][0])
+        s2 = int(ours["counts"][5:9].sum())
+        passes = ours["passes"]
+        S = 16 if dt == "f64" else 8
+        rec = 12                     # record: 8-byte sort key + 4-byte value
+        big_bytes = rec * s1 + passes * 2 * rec * s1 + (4 + S) * s1 + (S + 4) * s2 if passes else 0
+        big_ms = st_ms.get("big", 0.0)
+        entry = {"config": desc, "n": n, "dtype": dt, "ms_per_hull": ms, "mpoints_s": n / ms / 1e3,
+                 "hull_size": h, "stage_ms_per_hull": st_ms,
+                 "round1_paper": int(paper["counts"][0]), "round1": s1, "spa": s2,
+                 "identical_spa_both_modes": all(bool((a == b).all()) and len(a) == len(b)
+                                                 for a, b in zip(ours["spa"], paper["spa"])),
+                 "sort_path": "multi-block" if passes else "shared-memory",
+                 "radix_passes": passes}
+        if passes and big_ms > 0:
+            ach = big_bytes / (big_ms * 1e-3) / 1e9
+            entry["k_big_roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                       "frac": ach / hbm, "algorithmic_bytes": big_bytes,
+                                       "kernel_ms_per_launch": big_ms,
+                                       "note": "record buffers of this size are partly L2-resident"
+                                               if big_bytes < 120e6 else ""}
+        out[name] = entry
+        del pts, idx
+        torch.cuda.empty_cache()
+    return out
 
 
 # Sizes of the paper's randomly distributed point sets (Table 2).
@@ -417,8 +504,10 @@ def main():
     ap.add_argument("--survivors", action="store_true",
                     help="print the survivors-after-each-round table against n (Sec. 3.3) instead")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the degenerate, all-extreme circle and int32 configurations")
     ap.add_argument("--batched-sets", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=96,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered load (0: skip the serving measurement)")
     ap.add_argument("--kinds", default=",".join(KINDS),
                     help="comma-separated subset of square,disk,gauss (profiling runs)")
@@ -515,6 +604,12 @@ def main():
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_ms_per_launch": dom_ms,
                 "stage_ms_per_hull": stage_all}
+    # the whole step against the method's floor: two reads of every input
+    # point (the extremes must be known before the classification)
+    step_bytes = 2 * 16.0 * args.n * len(kinds)
+    roofline["step"] = {"algorithmic_bytes": step_bytes, "ms": ms_step,
+                        "achieved": step_bytes / (ms_step * 1e-3) / 1e9,
+                        "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm}
 
     # end to end through the host entry point (pinned host inputs)
     pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in kinds}
@@ -561,8 +656,11 @@ def main():
     torch.cuda.empty_cache()
     f32soa = f32soa_bench(cch, torch, host["square"], max(args.steps, 3)) if "square" in host else None
     torch.cuda.empty_cache()
+    extra = None if args.no_extra else extra_configs_bench(cch, torch, dev, max(args.steps // 2, 5), hbm)
+    torch.cuda.empty_cache()
     batched = None if args.no_batched else batched_bench(cch, torch, dev, stream, args.batched_sets)
-    serving = serve_bench(cch, args.serve_requests) if args.serve_requests > 0 else None
+    torch.cuda.empty_cache()
+    serving = serve_bench(cch, torch, dev, args.serve_requests) if args.serve_requests > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -573,6 +671,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
         "gpu_launches": launches, "batched": batched, "serving": serving, "f32soa": f32soa,
+        "configs": extra,
     }
     print(json.dumps(line), flush=True)
     if dist:

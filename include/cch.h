@@ -131,7 +131,13 @@ int cch_hull_f32soa(const float *x, const float *y, int64_t n, int32_t *out_idx,
  *   opts          bit 0: evaluate every float64 quadrilateral test exactly
  *                 (no FP32 filter); bit 1: keep every round-1 survivor (no
  *                 SPA-dominance prefilter, so r1_idx is exactly the paper's
- *                 R1..R4); other bits must be 0
+ *                 R1..R4); bit 2: the paper's chunked GPU SPA (Sec. 2.2.2:
+ *                 per region one block of 1024 threads, thread t checking
+ *                 sorted points [t L, (t+1) L), L = ceil(m / 1024), with
+ *                 Fig. 2's rule restarted at its chunk's first point) gives
+ *                 spa_idx and its counts, on the paper's round-1 sets (bit 2
+ *                 implies bit 1; the hull still comes from the sequential
+ *                 rule, so out_idx is unchanged); other bits must be 0
  *   r1_idx        device int32[max(n,1)]: round-1 survivors (Sec. 2.1.1),
  *                 region after region, index order within a region
  *   r1_region     device int32[max(n,1)]: their regions 1..4
@@ -152,14 +158,15 @@ int cch_hull_stages(const void *points, int64_t n, int dtype, uint32_t opts,
 
 /*
  * Stage timing.  cch_profile(1) makes every later call record CUDA events on
- * its stream around seven stages: (0) the extremes pass a1, (1) the
+ * its stream around eight stages: (0) the extremes pass a1, (1) the
  * dominance-table sample, (2) the classify pass a2, (3) the gather of the
  * survivors into region order, (4) sort and SPA of the shared-memory path,
- * (5) sort and SPA of the multi-block path, (6) chain hull and output.
- * cch_profile_read synchronises on the recorded events, writes the summed
- * milliseconds per stage to stage_ms[0 .. min(7, max_stages)), the number of
- * calls to *calls (if not NULL), forgets them, and returns the number of
- * stages (7).  cch_profile(0) stops recording.  cch_profile_stages(mask)
+ * (5) sort and SPA of the multi-block path, (6) chain hull and output,
+ * (7) the stage extraction of cch_hull_stages (with opts bit 2: the paper's
+ * chunked SPA).  cch_profile_read synchronises on the recorded events, writes
+ * the summed milliseconds per stage to stage_ms[0 .. min(8, max_stages)), the
+ * number of calls to *calls (if not NULL), forgets them, and returns the
+ * number of stages (8).  cch_profile(0) stops recording.  cch_profile_stages(mask)
  * records only around the stages whose bit is set in mask (bit k: stage k;
  * the others read as 0), which keeps the events' own cost out of the rest
  * of the pipeline; mask 0 stops recording.
@@ -240,6 +247,16 @@ int cch_serve_create(const cch_serve_config *cfg, cch_server **out);
  * CCH_ERR_RANGE if the request alone exceeds the budget, CCH_ERR_BUSY if
  * the queue is full. */
 int cch_serve_submit(cch_server *srv, const void *points, int64_t n, uint64_t *ticket);
+/* Queue one request whose points are in DEVICE memory ([n,2] of the
+ * server's dtype, 8/16-byte aligned): they are copied, device to device and
+ * ordered after the caller's earlier work on `stream`, into a resident
+ * buffer the server owns; the copy is complete when the call returns, so the
+ * caller may reuse or free its buffer at once.  The request then stays in
+ * device memory until its batch has read it (no host copy on the way).  The
+ * resident copies of queued requests are not part of the budget, which
+ * covers the batches being computed.  Errors as cch_serve_submit. */
+int cch_serve_submit_device(cch_server *srv, const void *points, int64_t n, void *stream,
+                            uint64_t *ticket);
 /* Non-blocking: up to `max` finished requests into done[0 .. *n_done). */
 int cch_serve_poll(cch_server *srv, cch_done *done, int max, int *n_done);
 /* Free a finished request's result. */

@@ -14,6 +14,9 @@ Contents
   * ``orient(a, b, c)``   -- the exact orientation predicate used by both.
   * ``bruteforce``        -- O(n^3) hull and O(n^2) SPA by exact rationals, the
     pins for the C code.
+  * ``blocked_spa(points)`` -- the SPA of the paper's GPU implementation
+    (Sec. 2.2.2): each region's sorted points in 1024 consecutive chunks,
+    Fig. 2's rule restarted at every chunk's first point.
   * ``parallel_hull(points)`` -- the multi-core CPU baseline the benchmark
     times beside the oracle (OpenMP: octagon filter, parallel merge sort,
     Andrew's chain; ``cch_cpu_parallel.c`` includes the oracle's source for
@@ -216,3 +219,46 @@ def method(points) -> dict:
         "spa": split(spa, spac),
         "hull": hl[:h].copy(),
     }
+
+
+# ------------------------------------------------- the paper's blocked SPA
+
+def blocked_spa(points, nchunks: int = 1024, m: dict | None = None) -> list:
+    """SPA as the paper's GPU implementation runs it (Sec. 2.2.2): one thread
+    block of BLOCK_SIZE = 1024 threads per region; thread t checks the
+    consecutive points [t L, (t + 1) L) of the region's sorted points,
+    L = ceil(m / 1024), with Fig. 2's rule -- a point is discarded when its
+    compared coordinate is strictly worse than the running value t, and t
+    takes every kept point's value -- restarted at the chunk's first point
+    (which is kept).  The region arrays of Sec. 2.2.2 hold the region's
+    points only (the extremes are interior, R0), so chunk 0 also starts at
+    its own first point.
+
+    Returns a list of 4 int32 arrays: the kept points of R1..R4 in sorted
+    (Table 1) order.  Compared coordinates (Fig. 2): R1 keeps y <= t, R2 keeps
+    x >= t, R3 keeps y >= t, R4 keeps x <= t; written here as one "smaller is
+    better" value v (R1 y, R2 -x, R3 -y, R4 x), a point is kept iff v is at
+    most the minimum of v over the earlier points of its chunk.
+    ``m`` may pass a precomputed ``method(points)``."""
+    p, _ = _prep(points)
+    if m is None:
+        m = method(points)
+    out = []
+    for k in range(4):
+        s = m["sorted"][k]
+        n = len(s)
+        if n == 0:
+            out.append(np.zeros(0, dtype=np.int32))
+            continue
+        coord = p[s, 1] if k in (0, 2) else p[s, 0]
+        v = -coord if k in (1, 2) else coord
+        v = v.astype(np.float64) if p.dtype == np.float64 else v.astype(np.int64)
+        L = (n + nchunks - 1) // nchunks
+        keep = np.zeros(n, dtype=bool)
+        for lo in range(0, n, L):
+            c = v[lo:lo + L]
+            run = np.minimum.accumulate(c)
+            excl = np.concatenate(([c[0]], run[:-1]))     # the first point is its own start value
+            keep[lo:lo + L] = c <= excl
+        out.append(s[keep].astype(np.int32))
+    return out

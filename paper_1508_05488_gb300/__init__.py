@@ -90,6 +90,8 @@ def _load():
             getattr(lib, name).restype = ctypes.c_int
         lib.cch_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
         lib.cch_serve_submit.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.cch_serve_submit_device.restype = ctypes.c_int
+        lib.cch_serve_submit_device.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.cch_serve_poll.argtypes = [vp, ctypes.POINTER(Done), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.cch_serve_release.argtypes = [vp, ctypes.c_uint64]
         lib.cch_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -253,12 +255,17 @@ def hull_host_ptr(host_ptr: int, n: int, dtype_code: int, out_idx_ptr: int, out_
                                  _stream_handle(stream))
 
 
-def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None) -> dict:
+def stages(points, exact_only: bool = False, prefilter: bool = True, blocked: bool = False,
+           stream=None) -> dict:
     """Run one hull and return its intermediate sets (synchronises).
 
     exact_only  every float64 quadrilateral test in exact arithmetic (no FP32 filter)
     prefilter   drop SPA-dominated points already in round 1 (default); with
                 False the round-1 sets are exactly the paper's R1..R4
+    blocked     ``spa`` is the paper's chunked GPU SPA (Sec. 2.2.2: 1024
+                chunks per region, each restarting at its first point) on the
+                paper's round-1 sets (implies prefilter=False); the hull is
+                the same
 
     ``r1`` list of 4 int32 arrays (round-1 survivors per region, index order),
     ``spa`` list of 4 int32 arrays (SPA survivors per region, sorted order),
@@ -276,7 +283,7 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None
     out_count = torch.empty(1, dtype=torch.int32, device=dev)
     counts = np.zeros(11, dtype=np.int64)
     rc = _load().cch_hull_stages(points.data_ptr() if n else None, n, _dtype_code(points),
-                                 (1 if exact_only else 0) | (0 if prefilter else 2),
+                                 (1 if exact_only else 0) | (0 if prefilter else 2) | (4 if blocked else 0),
                                  r1.data_ptr(), r1r.data_ptr(),
                                  spa.data_ptr(), counts.ctypes.data, out_idx.data_ptr(),
                                  out_count.data_ptr(), _stream_handle(stream))
@@ -303,7 +310,7 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, stream=None
     }
 
 
-STAGE_NAMES = ("k_extremes", "k_stairs", "k_classify", "gather", "small", "big", "chain")
+STAGE_NAMES = ("k_extremes", "k_stairs", "k_classify", "gather", "small", "big", "chain", "blocked_spa")
 
 
 def profile(enable: bool = True):
@@ -321,9 +328,9 @@ def profile_stages(names) -> None:
 
 def profile_read() -> tuple[dict, int]:
     """Summed milliseconds per stage since the last read, and the call count."""
-    ms = np.zeros(8, dtype=np.float64)
+    ms = np.zeros(len(STAGE_NAMES), dtype=np.float64)
     calls = np.zeros(1, dtype=np.int64)
-    k = _load().cch_profile_read(ms.ctypes.data, 8, calls.ctypes.data)
+    k = _load().cch_profile_read(ms.ctypes.data, len(STAGE_NAMES), calls.ctypes.data)
     if k < 0:
         raise CchError(k, "cch_profile_read")
     return {STAGE_NAMES[i]: float(ms[i]) for i in range(k)}, int(calls[0])
@@ -346,9 +353,11 @@ class Server:
     """Hull server (cch_serve_*): requests are admitted by a device-memory
     budget and batched onto a pool of streams as they arrive.
 
-    ``submit`` copies a host ``[n, 2]`` array and returns a ticket; ``poll``
-    returns the finished requests as ``(ticket, status, hull, latency_ms)``
-    with ``hull`` a NumPy copy (the server's copy is released at once)."""
+    ``submit`` copies a ``[n, 2]`` array -- a host array, or a CUDA tensor,
+    which stays in device memory (cch_serve_submit_device, ordered after the
+    current stream) -- and returns a ticket; ``poll`` returns the finished
+    requests as ``(ticket, status, hull, latency_ms)`` with ``hull`` a NumPy
+    copy (the server's copy is released at once)."""
 
     def __init__(self, dtype=np.float64, budget_bytes: int = 0, num_streams: int = 0, max_pending: int = 0,
                  max_batch: int = 0):
@@ -361,7 +370,17 @@ class Server:
         _check(_load().cch_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "cch_serve_create")
         self._h = h
 
-    def submit(self, points) -> int:
+    def submit(self, points, stream=None) -> int:
+        if getattr(points, "is_cuda", False):
+            import torch
+            _check_points(points)
+            if points.dtype != (torch.float64 if self.dtype == np.float64 else torch.int32):
+                raise TypeError("device points must match the server's dtype")
+            t = ctypes.c_uint64()
+            _check(_load().cch_serve_submit_device(self._h, points.data_ptr() if points.shape[0] else None,
+                                                   points.shape[0], _stream_handle(stream), ctypes.byref(t)),
+                   "cch_serve_submit_device")
+            return int(t.value)
         p = np.ascontiguousarray(points, dtype=self.dtype)
         if p.ndim != 2 or p.shape[1] != 2:
             raise ValueError("points must be [n, 2]")

@@ -113,7 +113,7 @@ std::atomic<uint64_t> g_launches{0};
 
 // Optional stage timing: CUDA events around the stages of every call, read
 // back (and summed) by cch_profile_read.
-constexpr int kStages = 7;   // a1, stairs, a2, gather, small path, multi-block path, chain
+constexpr int kStages = 8;   // a1, stairs, a2, gather, small path, multi-block path, chain, blocked SPA
 struct ProfRec { cudaEvent_t ev[kStages + 1]; uint32_t mask; };
 uint32_t g_prof = 0;   // stages whose boundaries get events (bit k: stage k)
 std::vector<ProfRec> g_prof_pending, g_prof_free;
@@ -153,7 +153,7 @@ int acquire(cudaStream_t stream, const Dims& d, Workspace** out) {
       c.nsets = std::max(d.nsets, ws->cap.nsets);
       c.nchunk1 = std::max(d.nchunk1, ws->cap.nchunk1);
       c.ntile2 = std::max(d.ntile2, ws->cap.ntile2);
-      c = make_dims(c.N, c.nsets, c.nchunk1, (int32_t)std::max<int64_t>(c.ntile2, c.N / 2048 + c.nsets + 1));
+      c = make_dims(c.N, c.nsets, c.nchunk1, (int32_t)std::max<int64_t>(c.ntile2, c.N / kClsMinTile + c.nsets + 1));
       if (cudaStreamSynchronize(stream) != cudaSuccess) return CCH_ERR_CUDA;
       cudaFree(ws->dev);
       ws->dev = nullptr;
@@ -242,8 +242,12 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
   nk += launch_big(j, L.w, La);
   mark(6);
   nk += launch_chain(j, L.w, La);
-  if (stages) { launch_extract_spa(j, L.w, stages->spa_idx, stream); nk++; }
   mark(7);
+  if (stages) {
+    if (j.opts & OPT_BLOCKED_SPA) nk += launch_spa_blocked(j, L.w, stages->spa_idx, stream);
+    else { launch_extract_spa(j, L.w, stages->spa_idx, stream); nk++; }
+  }
+  mark(8);
   if (ev) g_prof_pending.push_back(rec);
   g_launches += (uint64_t)nk;
   if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
@@ -494,7 +498,8 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   int st = check_common(points, n, dtype, out_idx, out_count);
   if (st != CCH_OK) return st;
   if (!r1_idx || !r1_region || !spa_idx || !counts_host) return CCH_ERR_INVALID;
-  if (opts & ~(uint32_t)(OPT_NO_FILTER | OPT_NO_PREFILTER)) return CCH_ERR_INVALID;
+  if (opts & ~(uint32_t)(OPT_NO_FILTER | OPT_NO_PREFILTER | OPT_BLOCKED_SPA)) return CCH_ERR_INVALID;
+  if (opts & OPT_BLOCKED_SPA) opts |= OPT_NO_PREFILTER;   // the paper's round-1 sets
   Job j = single_job(points, n, dtype, out_idx, out_count, opts);
   StageOut so{r1_idx, r1_region, spa_idx};
   Workspace* ws = nullptr;
@@ -509,7 +514,7 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   if (cudaStreamSynchronize(s) != cudaSuccess) return CCH_ERR_CUDA;
   counts_host[0] = c.s1;
   for (int r = 0; r < 4; r++) counts_host[1 + r] = c.cnt[r];
-  for (int r = 0; r < 4; r++) counts_host[5 + r] = c.s2[r];
+  for (int r = 0; r < 4; r++) counts_host[5 + r] = (opts & OPT_BLOCKED_SPA) ? c.sb[r] : c.s2[r];
   counts_host[9] = c.status != 0 ? c.status : (int32_t)ctr[CT_ERR];
   counts_host[10] = c.passes;
   return CCH_OK;

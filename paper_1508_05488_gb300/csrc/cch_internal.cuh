@@ -42,11 +42,13 @@ enum : int { DT_I32 = 1, DT_F64 = 2 };
 // ------------------------------------------------------------------ sizes
 constexpr int kThreads = 256;          // every kernel runs 256-thread CTAs
 constexpr int kWarps = kThreads / 32;
-// a2 tiles are 32 KB of points: 2048 float64 or 4096 int32 points
-constexpr int kClsTileBytes = 32768;
+// a2 tiles (points; a multiple of 32 x kClsConsumers): one TMA stage each
+constexpr int kClsTileF64 = 2048;      // 32 KB
+constexpr int kClsTileI32 = 4096;      // 32 KB
 constexpr int kClsStages = 2;          // TMA ring depth of a2
 constexpr int kClsConsumers = 8;       // consumer warps of a2: each tile has 8 sub-slots
-__host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? 2048 : 4096; }
+__host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? kClsTileF64 : kClsTileI32; }
+constexpr int kClsMinTile = kClsTileF64 < kClsTileI32 ? kClsTileF64 : kClsTileI32;
 // SPA-dominance prefilter ("stairs"): per region, the prefix minimum of the
 // compared coordinate over buckets of the sort coordinate, built from a
 // sample of the set.
@@ -90,6 +92,8 @@ enum : uint32_t {
   SF_STAIRS = 4u,       // the dominance prefilter is active for this set
   SF_BIG = 8u,          // some region exceeds kSmallMax survivors: multi-CTA sort
   SF_SMALL = 256u,      // float64 set with every coordinate below 2^60: FP32 views valid
+  SF_SHORTVIEW = 512u,  // float64 set with every coordinate's magnitude in [2^-126, 2^60]
+  SF_LOCALOUT = 1024u,  // every chain of the set fits one chain block: k_chain_local writes the output
   SF_DEGEN0 = 16u,      // bit SF_DEGEN0 << k: E_k and E_{k+1} are the same point
 };
 
@@ -148,6 +152,7 @@ struct Job {
 enum : uint32_t {
   OPT_NO_FILTER = 1u,     // force the exact path for every f64 quadrilateral test
   OPT_NO_PREFILTER = 2u,  // keep every round-1 survivor (the paper's round 1 as printed)
+  OPT_BLOCKED_SPA = 4u,   // stage output: the paper's chunked GPU SPA (Sec. 2.2.2); implies OPT_NO_PREFILTER
 };
 
 __device__ __forceinline__ SetDesc get_set(const Job& j, int s) {
@@ -158,8 +163,8 @@ __device__ __forceinline__ SetDesc get_set(const Job& j, int s) {
 struct Part {
   uint64_t k1[4], k2[4];
   uint32_t idx[4];
-  uint32_t bad;          // 1: non-finite seen, 2: magnitude out of range
-  uint32_t pad;
+  uint32_t bad;          // smallest top-word magnitude of a nonzero coordinate (float64)
+  uint32_t lomag;        // the same over every coordinate, zeros included
 };
 
 // Device-resident per-set state (zeroed every call).
@@ -179,6 +184,10 @@ struct SetCtl {
   float    bx0, bx1, by0, by1;          // dominance box (FP32 views, open; empty when zero)
   uint32_t arrive3;          // stairs chunk arrivals
   uint32_t passes;           // radix passes the multi-block sort ran for this set
+  uint32_t nloc;             // SF_LOCALOUT: chain blocks (= chains) of the set
+  uint32_t arrive5;          // SF_LOCALOUT: chain blocks done
+  uint32_t nal[4];           // SF_LOCALOUT: output points of chain r (its kept positions but the last)
+  uint32_t sb[4];            // OPT_BLOCKED_SPA: points the chunked SPA keeps per region
 };
 
 // SPA prefix-minimum look-back status of one tile: value words published
@@ -787,6 +796,7 @@ int launch_big(const Job& j, const Ws& w, const Launch& L);
 int launch_chain(const Job& j, const Ws& w, const Launch& L);
 // stage extraction (cch_hull_stages)
 void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
+int launch_spa_blocked(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
 int extremes_blocks_per_sm(int dtype);
 void count_launches(uint64_t n);   // add to the library's launch counter (cch_launch_count)
 void serve_release_pinned();   // free the server's pooled pinned host buffers

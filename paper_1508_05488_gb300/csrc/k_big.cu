@@ -137,6 +137,26 @@ __device__ void plan_chain(const Job& j, const Ws& w) {
         to = (L - 1 + kOutTile - 1) / kOutTile;
       }
     }
+    // A set whose chains each fit one chain block takes its output from
+    // k_chain_local (the last of its chain blocks writes it): no output
+    // tiles.  The four threads of a set are neighbouring lanes of one warp.
+    {
+      uint32_t f = tb <= 1u ? 1u : 0u;
+      f &= __shfl_xor_sync(0xFFFFFFFFu, f, 1);   // every lane takes part in both shuffles
+      f &= __shfl_xor_sync(0xFFFFFFFFu, f, 2);
+      const bool fit = f != 0u;
+      uint32_t nb = tb;
+      nb += __shfl_xor_sync(0xFFFFFFFFu, nb, 1);
+      nb += __shfl_xor_sync(0xFFFFFFFFu, nb, 2);
+      if (g < nseg && fit && nb > 0) {
+        to = 0;
+        if ((g & 3) == 0) {
+          SetCtl& cw = w.ctl[g >> 2];
+          cw.flags |= SF_LOCALOUT;
+          cw.nloc = nb;
+        }
+      }
+    }
     uint32_t x = tb, y = to;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -533,6 +553,110 @@ __global__ void __launch_bounds__(kThreads) k_big(Job j, Ws w) {
   big_spa<DT>(j, w);
   if (!grid_sync(w, gen)) return;
   if (blockIdx.x == 0) plan_chain(j, w);
+}
+
+// ------------------------------------------- the paper's blocked SPA
+//
+// Comparison mode of cch_hull_stages (OPT_BLOCKED_SPA): SPA as the paper's
+// GPU implementation runs it (Sec. 2.2.2): one thread block of 1024 threads
+// per region, thread t checking the consecutive sorted points
+// [t L, (t + 1) L), L = ceil(m / 1024), with Fig. 2's rule restarted at its
+// chunk's first point (kept).  The region arrays of the paper hold the
+// region's points only (the extremes are R0), so chunk 0 starts at its own
+// first point too.  In this mode every set takes the multi-block sort, so
+// the sorted records are in global memory; the chunked rule reads them
+// after the pipeline and reports its survivors, while the hull itself comes
+// from the exact sequential rule (a superset of its survivors would give the
+// same hull).  Two kernels: the check (per record a keep byte, per region the
+// count) and the stable compaction of the kept records' indices.
+constexpr int kBlkThreads = 1024;
+
+template <int DT>
+__device__ __forceinline__ const uint32_t* sorted_vals(const Job& j, const Ws& w, const SetCtl& c) {
+  const uint32_t* gh = w.hist;          // set 0
+  int par = 0;
+  for (int q = 0; q < kSortPasses; q++)
+    par ^= __syncthreads_or(gh[q * 256 + (threadIdx.x & 255)] == c.s1) ? 0 : 1;
+  return par ? w.valB : w.valA;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBlkThreads) k_spa_blocked(Job j, Ws w) {
+  griddep_enter();
+  using P = typename PtT<DT>::T;
+  __shared__ uint32_t wsum[kBlkThreads / 32];
+  const int r = blockIdx.x;                       // set 0, region r
+  const SetDesc sd = get_set(j, 0);
+  const SetCtl& c = w.ctl[0];
+  if (c.status != 0 || !(c.flags & SF_BIG)) return;   // uniform
+  const uint32_t* vin = sorted_vals<DT>(j, w, c);
+  uint32_t roff = 0;
+  for (int q = 0; q < r; q++) roff += c.cnt[q];
+  const uint32_t m = c.cnt[r];
+  const uint32_t L = (m + kBlkThreads - 1) / kBlkThreads;
+  const uint32_t b0 = threadIdx.x * L, b1 = min(m, b0 + L);
+  const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
+  uint8_t* keep = reinterpret_cast<uint8_t*>(w.spvB) + sd.off + roff;
+  uint64_t t = 0;
+  uint32_t kept = 0;
+  for (uint32_t i = b0; i < b1; i++) {
+    const uint64_t v = spa_value<DT>(pts[vin[sd.off + roff + i] & kIdxMask], r);
+    const bool k = i == b0 || v <= t;              // Fig. 2: discard only the strictly worse
+    if (k) { t = v; kept++; }
+    keep[i] = k ? 1 : 0;
+  }
+  const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, kept);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t a = 0;
+    for (int q = 0; q < kBlkThreads / 32; q++) a += wsum[q];
+    w.ctl[0].sb[r] = a;
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBlkThreads) k_spa_blocked_out(Job j, Ws w, int32_t* spa_idx) {
+  griddep_enter();
+  __shared__ uint32_t wsum[kBlkThreads / 32];
+  const int r = blockIdx.x;
+  const SetDesc sd = get_set(j, 0);
+  const SetCtl& c = w.ctl[0];
+  if (c.status != 0 || !(c.flags & SF_BIG)) return;
+  const uint32_t* vin = sorted_vals<DT>(j, w, c);
+  uint32_t roff = 0, ooff = 0;
+  for (int q = 0; q < r; q++) { roff += c.cnt[q]; ooff += c.sb[q]; }
+  const uint32_t m = c.cnt[r];
+  const uint32_t L = (m + kBlkThreads - 1) / kBlkThreads;
+  const uint32_t b0 = threadIdx.x * L, b1 = min(m, b0 + L);
+  const uint8_t* keep = reinterpret_cast<const uint8_t*>(w.spvB) + sd.off + roff;
+  uint32_t n = 0;
+  for (uint32_t i = b0; i < b1; i++) n += keep[i];
+  // exclusive prefix of n over the block (thread order = chunk order)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  uint32_t pos = ooff + x - n;
+  for (int q = 0; q < warp; q++) pos += wsum[q];
+  for (uint32_t i = b0; i < b1; i++)
+    if (keep[i]) spa_idx[pos++] = (int32_t)(vin[sd.off + roff + i] & kIdxMask);
+}
+
+int launch_spa_blocked(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st) {
+  if (j.dtype == DT_F64) {
+    launch_pdl(k_spa_blocked<DT_F64>, 4, kBlkThreads, 0, st, j, w);
+    launch_pdl(k_spa_blocked_out<DT_F64>, 4, kBlkThreads, 0, st, j, w, spa_idx);
+  } else {
+    launch_pdl(k_spa_blocked<DT_I32>, 4, kBlkThreads, 0, st, j, w);
+    launch_pdl(k_spa_blocked_out<DT_I32>, 4, kBlkThreads, 0, st, j, w, spa_idx);
+  }
+  return 2;
 }
 
 int launch_big(const Job& j, const Ws& w, const Launch& L) {

@@ -156,6 +156,24 @@ __device__ __forceinline__ int block_compact(const uint8_t* al, int m, uint16_t*
   return n;
 }
 
+// Output of a set whose chains each fit one chain block (SF_LOCALOUT), by the
+// last of its k_chain_local blocks: every block has left the indices of its
+// chain's kept positions but the last (the next chain's first) compacted at
+// the start of the chain's link slots (cprev) and their number in nal[r];
+// the four lists are copied in order R1..R4 into out_idx (coalesced reads
+// from L2: they were published before their blocks' arrival).
+__device__ void chain_set_output(const Job& j, const Ws& w, const SetDesc& sd, int s, const SetCtl& c) {
+  uint32_t off = 0;
+#pragma unroll 1
+  for (int r = 0; r < 4; r++) {
+    const uint32_t nr = __ldcg(&c.nal[r]);
+    const uint32_t* src = w.cprev + chain_base(sd, s, c, r);
+    for (uint32_t k = threadIdx.x; k < nr; k += kThreads) j.out_idx[sd.off + off + k] = (int32_t)__ldcg(src + k);
+    off += nr;
+  }
+  if (threadIdx.x == 0) j.out_counts[s] = (int32_t)off;
+}
+
 template <int DT>
 constexpr size_t chain_local_smem() {
   return (size_t)kChainBlk * (sizeof(typename PT<DT>::T) + (DT == DT_F64 ? 16 : 0) + 2 + 2 + 2 + 1) +
@@ -177,6 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
   uint8_t* al = reinterpret_cast<uint8_t*>(gt + kThreads);
   __shared__ P pred;
   __shared__ int sh_cnt[kWarps + 1];
+  __shared__ int sh_last;
 
   const uint32_t total = w.ctr[CT_CHAIN_TOTAL];
   P* cp = reinterpret_cast<P*>(w.cpts);
@@ -311,6 +330,25 @@ __global__ void __launch_bounds__(kThreads) k_chain_local(Job j, Ws w) {
       }
     }
     __syncthreads();
+    if (c.flags & SF_LOCALOUT) {      // uniform: this block is all of chain r (p0 = 0, m = L)
+      // the indices of the kept positions but the last, in order, at the
+      // start of the chain's link slots (no merge or output pass follows)
+      const int nout = block_compact(al, m - 1, stk, sh_cnt);
+      for (int k = threadIdx.x; k < nout; k += kThreads) w.cprev[cb + k] = w.cidx[cb + stk[k]];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        w.ctl[s].nal[r] = (uint32_t)nout;
+        __threadfence();
+        sh_last = atomicAdd(&w.ctl[s].arrive5, 1u) == c.nloc - 1u;
+      }
+      __syncthreads();
+      if (sh_last) {
+        __threadfence();
+        chain_set_output(j, w, sd, s, c);
+      }
+      __syncthreads();
+      continue;
+    }
     for (int i = threadIdx.x; i < m; i += kThreads) {
       w.calive[cb + p0 + i] = al[i];
       if (al[i]) {
@@ -365,6 +403,16 @@ __global__ void __launch_bounds__(kThreads) k_output(Job j, Ws w) {
   const uint32_t total = w.ctr[CT_OUT_TOTAL];
   const uint32_t tag = (j.epoch << 4) | 12u;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  if (total == 0) {
+    // every output was written before this kernel (by k_chain_local or the
+    // chain plan): one CTA applies a device error of the call, if any
+    if (blockIdx.x == 0) {
+      const int err = (int)ld_acq_u32(w.ctr + CT_ERR);
+      if (err != 0)
+        for (int s = threadIdx.x; s < j.nsets; s += kThreads) j.out_counts[s] = err;
+    }
+    return;
+  }
   for (;;) {
     if (threadIdx.x == 0) sh_tile = atomicAdd(w.ctr + CT_OUT_TILE, 1u);
     __syncthreads();

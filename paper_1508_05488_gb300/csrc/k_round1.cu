@@ -22,10 +22,12 @@
 // edges), so P is not an SPA survivor of the full set and dropping it early
 // leaves the SPA survivors -- and the hull -- unchanged.  k_stairs buckets a
 // sample by the sort coordinate (monotone FP32 map) and keeps per bucket the
-// best compared coordinate (top 32 key bits); the prefix minimum over lower
-// buckets, seeded with the region's first extreme, gives for every bucket a
-// value such that any region point of that bucket with a larger value is
-// dominated by a sample point of a strictly lower bucket.
+// best compared coordinate, as the order word of its FP32 view (the view is
+// non-decreasing in the coordinate, so a strictly larger word means a
+// strictly worse coordinate); the prefix minimum over lower buckets, seeded
+// with the region's first extreme, gives for every bucket a word such that
+// any region point of that bucket with a larger word is dominated by a
+// sample point of a strictly lower bucket.
 //
 // Dominance box.  The same argument in all four quadrants at once: k_stairs
 // also picks the sample point furthest into each quadrant (smallest x+y,
@@ -47,10 +49,12 @@ struct PointT<DT_I32> { using T = int2; };
 
 // ------------------------------------------------------------- keys
 
-// Top word of the smallest magnitude the float64 domain takes, 2^-400, read
-// as FP32 (0x26F00000): a coordinate whose top word reads below it in
-// magnitude is zero or possibly too small, and gets the exact test.
-constexpr uint32_t kTinyTopBits = (1023u - 400u) << 20;
+// Top word of 2^-126, read as FP32: a coordinate whose top word reads below
+// it in magnitude is zero or below 2^-126 in magnitude, and gets the exact
+// bookkeeping -- the lower end of the domain check (nonzero magnitudes below
+// 2^-400 are out of range) and the smallest top-word magnitude of the set,
+// zeros included, which tells a2 whether its short FP32 view is valid.
+constexpr uint32_t kTinyTopBits = (1023u - 126u) << 20;
 #define kTinyTopF __uint_as_float(kTinyTopBits)
 
 // Order-preserving key of a float64 as 32-bit words (-0.0 -> +0.0).  Also
@@ -216,6 +220,26 @@ __device__ __forceinline__ void f32_view(const typename PointT<DT>::T& p, float&
   }
 }
 
+// The same FP32 view in three integer operations per coordinate, for sets
+// whose coordinates all have magnitude in [2^-126, 2^60] (SF_SHORTVIEW): the
+// exponent is rebiased on the signed top word (no borrow reaches the sign:
+// the magnitude's top word is at least 0x38100000) and shifted with the three
+// leading bits of the low word; the bits equal f64_trunc_f32's.
+__device__ __forceinline__ float f64_view_short(uint64_t b) {
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t t = hi - 0x38000000u;
+  return __uint_as_float(__funnelshift_l(lo, t, 3) | (hi & 0x80000000u));
+}
+template <int DT, bool SHORT>
+__device__ __forceinline__ void f32_view_a2(const typename PointT<DT>::T& p, float& X, float& Y) {
+  if constexpr (DT == DT_F64 && SHORT) {
+    X = f64_view_short((uint64_t)__double_as_longlong(p.x));
+    Y = f64_view_short((uint64_t)__double_as_longlong(p.y));
+  } else {
+    f32_view<DT>(p, X, Y);
+  }
+}
+
 // Compared-coordinate key (top word) of region r (0..3) in "smaller is
 // better" form: R1 y, R2 -x, R3 -y, R4 x.
 template <int DT>
@@ -236,6 +260,15 @@ __device__ __forceinline__ uint32_t cmp_key_hi(const typename PointT<DT>::T& p, 
   }
 }
 
+// Compared coordinate of region r (0..3) as the order word of its FP32 view
+// in "smaller is better" form: R1 y, R2 -x, R3 -y, R4 x (-0.0 read as +0.0).
+// The view is non-decreasing in the coordinate, so a strictly larger word
+// means a strictly worse coordinate: the dominance tables hold these words.
+__device__ __forceinline__ uint32_t cmp_view_order(float X, float Y, int r) {
+  const float v = (r & 1) ? X : Y;
+  return f32_order(__fadd_rn((r == 1 || r == 2) ? -v : v, 0.0f));
+}
+
 // Sort coordinate (FP32 view) of region r: R1 x asc, R2 y asc, R3 x desc, R4 y desc.
 __device__ __forceinline__ float sort_u(float X, float Y, int r) {
   switch (r) {
@@ -249,7 +282,7 @@ __device__ __forceinline__ float sort_u(float X, float Y, int r) {
 // Edge set-up of one set, run by one thread once E1..E4 are known.
 template <int DT>
 __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, const Lex best[4],
-                          uint32_t amin) {
+                          uint32_t amin, uint32_t lomag) {
   SetCtl& c = w.ctl[s];
   using P = typename PointT<DT>::T;
   const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
@@ -291,6 +324,9 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
     const double lim = 1152921504606846976.0;  // 2^60
     small = xm <= lim && ym <= lim;
     if (small) flags |= SF_SMALL;
+    // every coordinate of magnitude in [2^-126, 2^60]: the short FP32 view
+    // (f32_view_short) equals f64_trunc_f32
+    if (small && lomag >= kTinyTopBits) flags |= SF_SHORTVIEW;
     const bool filt = small && !(j.opts & OPT_NO_FILTER);
     if (filt) flags |= SF_FILTER;
     // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
@@ -340,7 +376,8 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
 
 constexpr int kExtStages = 3;                          // TMA ring depth of a1
 constexpr int kExtBlock = (kClsConsumers + 1) * 32;    // 8 consumer warps + a producer warp
-constexpr int kExtSmem = kExtStages * (kClsTileBytes + 16);
+constexpr int kExtTileBytes = 32768;                    // a1 tiles: 2048 float64 / 4096 int32 points
+constexpr int kExtSmem = kExtStages * (kExtTileBytes + 16);
 
 // Barrier of the consumer warps only (the producer warp has left).
 __device__ __forceinline__ void consumers_sync() {
@@ -357,15 +394,15 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
   constexpr int PB = (int)sizeof(P);
-  constexpr int TILE = kClsTileBytes / PB;
+  constexpr int TILE = kExtTileBytes / PB;
   constexpr int WPTS = TILE / kClsConsumers;
   constexpr int IW = WPTS / 32;
-  constexpr int SB = kClsTileBytes + 16;
+  constexpr int SB = kExtTileBytes + 16;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kExtStages], empty[kExtStages];
   __shared__ int st_head[kExtStages];
   __shared__ Lex red[kClsConsumers][4];
-  __shared__ uint32_t red_amin[kClsConsumers];
+  __shared__ uint32_t red_amin[kClsConsumers], red_lomag[kClsConsumers];
   __shared__ int last;
 
   const int chunk = blockIdx.x;
@@ -440,7 +477,8 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; th[k] = 0xFFFFFFFFu; }
   a1_thresholds_f(best, thf);
-  uint32_t amin = 0x7FFFFFFFu;
+  uint32_t amin = 0x7FFFFFFFu;      // smallest top-word magnitude of a nonzero coordinate
+  uint32_t lomag = 0x7FFFFFFFu;     // the same over every coordinate, zeros included (float64)
   // set-local indices fit in 32 bits (n <= 2^30)
   for (int it = 0; it < ntile; it++) {
     const int slot = it % kExtStages;
@@ -486,8 +524,10 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
           if ((tinym >> k) & 1u) {
             uint32_t a = xh[k] & 0x7FFFFFFFu;
             if ((a | xl[k]) != 0) amin = min(amin, a);
+            lomag = min(lomag, a);
             a = yh[k] & 0x7FFFFFFFu;
             if ((a | yl[k]) != 0) amin = min(amin, a);
+            lomag = min(lomag, a);
           }
         }
       }
@@ -540,21 +580,25 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
 #pragma unroll
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
     amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
+    lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
   }
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
     red_amin[warp] = amin;
+    red_lomag[warp] = lomag;
   }
   consumers_sync();
   if (tid == 0) {
     for (int q = 1; q < kClsConsumers; q++) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
       amin = min(amin, red_amin[q]);
+      lomag = min(lomag, red_lomag[q]);
     }
     Part& pt = w.part[chunk];
     for (int k = 0; k < 4; k++) { pt.k1[k] = best[k].k1; pt.k2[k] = best[k].k2; pt.idx[k] = best[k].idx; }
     pt.bad = amin;
+    pt.lomag = lomag;
     __threadfence();
     last = atomicAdd(&w.ctl[s].arrive1, 1u) == (uint32_t)(sd.nchunk1 - 1);
   }
@@ -571,6 +615,7 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
   amin = 0x7FFFFFFFu;
+  lomag = 0x7FFFFFFFu;
   for (int q = threadIdx.x; q < sd.nchunk1; q += kClsConsumers * 32) {
     const Part& pt = w.part[sd.chunk1 + q];
     for (int k = 0; k < 4; k++) {
@@ -578,26 +623,30 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
       lex_min_into(best[k], v);
     }
     amin = min(amin, pt.bad);
+    lomag = min(lomag, pt.lomag);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
     amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
+    lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
   }
   consumers_sync();
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
     red_amin[warp] = amin;
+    red_lomag[warp] = lomag;
   }
   consumers_sync();
   if (threadIdx.x == 0) {
     for (int q = 1; q < kClsConsumers; q++) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
       amin = min(amin, red_amin[q]);
+      lomag = min(lomag, red_lomag[q]);
     }
-    setup_set<DT>(j, w, s, sd, best, amin);
+    setup_set<DT>(j, w, s, sd, best, amin, lomag);
   }
 }
 
@@ -684,7 +733,7 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
       for (int r = 0; r < 4; r++) {
         float su = sort_u(X, Y, r);
         if (su >= lo[r] && su <= hi[r])
-          atomicMin(&tb[r][stair_pad(stair_bucket(su, lo[r], sc[r]))], cmp_key_hi<DT>(v[u], r));
+          atomicMin(&tb[r][stair_pad(stair_bucket(su, lo[r], sc[r]))], cmp_view_order(X, Y, r));
       }
     }
   }
@@ -756,7 +805,9 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
     P e;
     if constexpr (DT == DT_F64) { e.x = c.ex[rr]; e.y = c.ey[rr]; }
     else { e.x = (int)c.ex[rr]; e.y = (int)c.ey[rr]; }
-    uint32_t ex = min(region_excl_min(mn, sw), cmp_key_hi<DT>(e, rr));
+    float EX, EY;
+    f32_view<DT>(e, EX, EY);
+    uint32_t ex = min(region_excl_min(mn, sw), cmp_view_order(EX, EY, rr));
     uint4 o[4];
 #pragma unroll
     for (int q = 0; q < 16; q++) {
@@ -859,7 +910,7 @@ constexpr int kClsBlock = (kClsConsumers + 1) * 32;  // + one producer warp
 
 template <int DT>
 constexpr int cls_smem_bytes() {
-  return kClsStages * (kClsTileBytes + 16);
+  return kClsStages * (cls_tile(DT) * (DT == DT_F64 ? 16 : 8) + 16);
 }
 
 // Set parameters a consumer warp keeps in registers (the per-point filter);
@@ -875,6 +926,35 @@ struct WarpParams {
   int ix[4], iy[4];
 };
 
+// a2 pass 1 of a float64 tile slice (items k = 0 .. IW-1 of this lane, point
+// wb + 32 k + lane): bit k of the result is set unless the point is certainly
+// inside the quadrilateral (FP32 filter of the four edges) or strictly inside
+// the dominance box; the point's FP32 view goes to vbw[32 k + lane].  SHORT
+// selects the three-operation FP32 view.
+template <bool SHORT, int IW>
+__device__ __forceinline__ uint32_t a2_pass1_f64(const unsigned char* base, int wb, int lane, int npv,
+                                                 const ClsParams& cp, uint2* vbw) {
+  uint32_t nim = 0;
+#pragma unroll 4
+  for (int k = 0; k < IW; k++) {
+    const int i = wb + k * 32 + lane;
+    if (i < npv) {
+      const double2 p = *reinterpret_cast<const double2*>(base + i * 16);
+      float X, Y;
+      f32_view_a2<DT_F64, SHORT>(p, X, Y);
+      vbw[k * 32 + lane] = make_uint2(__float_as_uint(X), __float_as_uint(Y));
+      const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
+      const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
+      const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
+      const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
+      const bool in = ((d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3])) |
+                      ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1));
+      nim |= (uint32_t)(!in) << k;
+    }
+  }
+  return nim;
+}
+
 // a2.  Warp-specialised: warp 8 acquires tiles (in increasing order) and
 // streams them into a ring of shared-memory stages with 1-D TMA bulk copies
 // (full/empty mbarriers); warps 0..7 each classify a contiguous eighth of the
@@ -886,15 +966,17 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
   constexpr int PB = (int)sizeof(P);
-  constexpr int TILE = kClsTileBytes / PB;
+  constexpr int TILE = cls_tile(DT);
+  static_assert(TILE % (32 * kClsConsumers) == 0, "a tile is a whole number of items per consumer lane");
   constexpr int WPTS = TILE / kClsConsumers;          // points per consumer warp
   constexpr int IW = WPTS / 32;                       // items per lane
-  constexpr int SB = kClsTileBytes + 16;              // stage bytes (16 bytes of slack in front)
+  static_assert(IW <= 16, "pass-2 queue entries hold the item in 4 bits");
+  constexpr int SB = TILE * PB + 16;                  // stage bytes (16 bytes of slack in front)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kClsStages], empty[kClsStages];
   __shared__ int st_tile[kClsStages], st_set[kClsStages], st_head[kClsStages];
   __shared__ uint16_t wq[kClsConsumers][IW * 32];     // pass-2 queue: int32 region << 9 | item << 5 | lane
-  __shared__ uint8_t wrk[kClsConsumers][IW * 32];     // pass-2 result: region of (item, lane)
+  __shared__ uint2 vb[kClsConsumers][IW * 32];         // views (float64) / points (int32) of the warp's slice
   __shared__ WarpParams wpar[kClsConsumers];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1007,27 +1089,26 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
     const int npv = cp.status != 0 ? 0 : np;
     const uint32_t* pre = w.stairs + (size_t)s * 4 * kStairB;
     const SetCtl& cg = w.ctl[s];
+    const bool shortv = (cp.flags & SF_SHORTVIEW) != 0;
 
     // pass 1, every point: is it certainly inside the quadrilateral?
-    // (float64: the FP32 filter's four edge tests; int32: the exact region)
+    // (float64: the FP32 filter's four edge tests; int32: the exact region).
+    // Every point's FP32 view (float64) or the point itself (int32) goes to
+    // the warp's view buffer, so that the stage can be released right after
+    // this pass and the producer refills it while pass 2 runs.
     uint32_t nim = 0;                              // items that need pass 2
     uint32_t ireg[IW > 8 ? 2 : 1] = {};            // int32: exact region, 4 bits per item
+    uint2* vbw = vb[warp];
+    if constexpr (DT == DT_F64) {
+      nim = shortv ? a2_pass1_f64<true, IW>(base, wb, lane, npv, cp, vbw)
+                   : a2_pass1_f64<false, IW>(base, wb, lane, npv, cp, vbw);
+    } else {
 #pragma unroll 4
-    for (int k = 0; k < IW; k++) {
-      const int i = wb + k * 32 + lane;
-      if (i < npv) {
-        const P p = *reinterpret_cast<const P*>(base + i * PB);
-        if constexpr (DT == DT_F64) {
-          float X, Y;
-          f32_view<DT>(p, X, Y);
-          const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
-          const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
-          const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
-          const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
-          const bool in = ((d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3])) |
-                          ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1));
-          nim |= (uint32_t)(!in) << k;
-        } else {
+      for (int k = 0; k < IW; k++) {
+        const int i = wb + k * 32 + lane;
+        if (i < npv) {
+          const P p = *reinterpret_cast<const P*>(base + i * PB);
+          vbw[k * 32 + lane] = make_uint2((uint32_t)p.x, (uint32_t)p.y);
           uint32_t r = 0;
           if (cp.flags & SF_WIDE) {
             r = 15u;
@@ -1046,12 +1127,19 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
         }
       }
     }
+    __syncwarp();
+    if (lane == 0)   // the warp is done with the stage: release it to the producer
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
+
     // pass 2, dense over the warp's remaining points (a queue): region,
-    // exact test where the filter was undecided, dominance prefilter
-    uint64_t regs = 0;
+    // exact test where the filter was undecided, dominance prefilter.  The
+    // queue lists the points in index order, so each round of 32 entries
+    // compacts its survivors into the warp's sub-slot of the tile in order.
+    // Only the rare exact test and the survivors' records read the point's
+    // exact coordinates (float64: again from global memory).
+    uint32_t rc01 = 0, rc23 = 0;                   // survivors of R1|R2, R3|R4 (16-bit fields)
     if (__any_sync(0xFFFFFFFFu, nim != 0)) {
       uint16_t* q = wq[warp];
-      uint8_t* rk = wrk[warp];
       uint32_t nq = 0;
 #pragma unroll
       for (int k = 0; k < IW; k++) {
@@ -1065,74 +1153,74 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
         nq += __popc(b);
       }
       __syncwarp();
-      for (uint32_t e = lane; e < nq; e += 32) {
-        const uint32_t en = q[e];
-        const int k = (int)(en >> 5) & 15, l = (int)(en & 31);
-        const P p = *reinterpret_cast<const P*>(base + (wb + k * 32 + l) * PB);
-        float X, Y;
-        f32_view<DT>(p, X, Y);
-        uint32_t r;
-        if constexpr (DT == DT_F64) {
-          const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
-          const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
-          const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
-          const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
-          // first edge not certainly inside decides: outside -> region,
-          // undecided -> exact test
-          r = !(d3 > cp.fE[3]) ? (d3 < -cp.fE[3] ? 4u : 15u) : 0u;
-          r = !(d2 > cp.fE[2]) ? (d2 < -cp.fE[2] ? 3u : 15u) : r;
-          r = !(d1 > cp.fE[1]) ? (d1 < -cp.fE[1] ? 2u : 15u) : r;
-          r = !(d0 > cp.fE[0]) ? (d0 < -cp.fE[0] ? 1u : 15u) : r;
-          if (r == 15u) r = (uint32_t)region_exact_f64(p.x, p.y, cg.ex, cg.ey, cp.flags);
-        } else {
-          r = (en >> 9) & 0xFu;
-          if (r == 15u) r = (uint32_t)region_exact_i32_wide(p.x, p.y, cg.ex, cg.ey, cp.flags);
-        }
-        if (r != 0 && (cp.flags & SF_STAIRS)) {
-          const int qr = (int)r - 1;
-          const int b = stair_bucket(sort_u(X, Y, qr), wp.slo[qr], wp.ssc[qr]);
-          if (cmp_key_hi<DT>(p, qr) > __ldg(pre + qr * kStairB + b)) r = 0;    // dominated
-        }
-        rk[k * 32 + l] = (uint8_t)r;
-      }
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < IW; k++)
-        if ((nim >> k) & 1u) regs |= (uint64_t)rk[k * 32 + lane] << (4 * k);
-    }
-    // warp-local stable compaction into the warp's sub-slot of the tile
-    uint32_t rc[4] = {0, 0, 0, 0};
-    if (__any_sync(0xFFFFFFFFu, regs != 0)) {
       const int64_t ob = sd.off + t0 + wb;
+      const P* gp = reinterpret_cast<const P*>(j.pts) + sd.off + t0;
       uint32_t run = 0;
-#pragma unroll
-      for (int k = 0; k < IW; k++) {
-        const int r = (int)((regs >> (4 * k)) & 0xFull);
+      for (uint32_t e0 = 0; e0 < nq; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        uint32_t r = 0;
+        int i = 0;
+        P p{};
+        if (e < nq) {
+          const uint32_t en = q[e];
+          const int slot_i = (int)((en >> 5) & 15) * 32 + (int)(en & 31);
+          i = wb + slot_i;
+          const uint2 v = vbw[slot_i];
+          float X, Y;
+          if constexpr (DT == DT_F64) {
+            X = __uint_as_float(v.x);
+            Y = __uint_as_float(v.y);
+            const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
+            const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
+            const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
+            const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
+            // first edge not certainly inside decides: outside -> region,
+            // undecided -> exact test
+            r = !(d3 > cp.fE[3]) ? (d3 < -cp.fE[3] ? 4u : 15u) : 0u;
+            r = !(d2 > cp.fE[2]) ? (d2 < -cp.fE[2] ? 3u : 15u) : r;
+            r = !(d1 > cp.fE[1]) ? (d1 < -cp.fE[1] ? 2u : 15u) : r;
+            r = !(d0 > cp.fE[0]) ? (d0 < -cp.fE[0] ? 1u : 15u) : r;
+            if (r == 15u) {
+              p = gp[i];
+              r = (uint32_t)region_exact_f64(p.x, p.y, cg.ex, cg.ey, cp.flags);
+            }
+          } else {
+            p.x = (int)v.x;
+            p.y = (int)v.y;
+            X = __int2float_rn(p.x);
+            Y = __int2float_rn(p.y);
+            r = (en >> 9) & 0xFu;
+            if (r == 15u) r = (uint32_t)region_exact_i32_wide(p.x, p.y, cg.ex, cg.ey, cp.flags);
+          }
+          if (r != 0 && (cp.flags & SF_STAIRS)) {
+            const int qr = (int)r - 1;
+            const int bk = stair_bucket(sort_u(X, Y, qr), wp.slo[qr], wp.ssc[qr]);
+            if (cmp_view_order(X, Y, qr) > __ldg(pre + qr * kStairB + bk)) r = 0;    // dominated
+          }
+        }
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
         if (r != 0) {
-          const int i = wb + k * 32 + lane;
-          const P p = *reinterpret_cast<const P*>(base + i * PB);
+          if constexpr (DT == DT_F64) p = gp[i];   // exact coordinates of a survivor
           const int64_t o = ob + run + __popc(b & lt_mask);
-          w.keyB[o] = sort_key<DT>(p, r);
-          w.valB[o] = ((uint32_t)(r - 1) << 30) | (uint32_t)(t0 + i);
-          if constexpr (DT == DT_F64) w.spvB[o] = spa_v_f64(p.x, p.y, r - 1);
-          else w.spvB[o] = spa_v_i32(p.x, p.y, r - 1);
-          rc[r - 1]++;
+          w.keyB[o] = sort_key<DT>(p, (int)r);
+          w.valB[o] = ((r - 1u) << 30) | (uint32_t)(t0 + i);
+          if constexpr (DT == DT_F64) w.spvB[o] = spa_v_f64(p.x, p.y, (int)r - 1);
+          else w.spvB[o] = spa_v_i32(p.x, p.y, (int)r - 1);
+          const uint32_t inc = 1u << (((r - 1u) & 1u) * 16u);
+          if (r <= 2u) rc01 += inc; else rc23 += inc;
         }
         run += __popc(b);
       }
-#pragma unroll
-      for (int q = 0; q < 4; q++) rc[q] = __reduce_add_sync(0xFFFFFFFFu, rc[q]);
+      rc01 = __reduce_add_sync(0xFFFFFFFFu, rc01);
+      rc23 = __reduce_add_sync(0xFFFFFFFFu, rc23);
     }
-    __syncwarp();
     if (lane == 0) {
-      // the warp is done with the stage: release it to the producer
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
-      w.tcnt[(size_t)tile * kClsConsumers + warp] =
-          (uint64_t)rc[0] | ((uint64_t)rc[1] << 16) | ((uint64_t)rc[2] << 32) | ((uint64_t)rc[3] << 48);
+      w.tcnt[(size_t)tile * kClsConsumers + warp] = (uint64_t)rc01 | ((uint64_t)rc23 << 32);
       uint32_t* pt = reinterpret_cast<uint32_t*>(w.ptot + sd.chunkP + (int)(lt / kPlanTiles));
-      for (int q = 0; q < 4; q++)
-        if (rc[q]) atomicAdd(pt + q, rc[q]);
+      if (rc01 & 0xFFFFu) atomicAdd(pt + 0, rc01 & 0xFFFFu);
+      if (rc01 >> 16) atomicAdd(pt + 1, rc01 >> 16);
+      if (rc23 & 0xFFFFu) atomicAdd(pt + 2, rc23 & 0xFFFFu);
+      if (rc23 >> 16) atomicAdd(pt + 3, rc23 >> 16);
     }
   }
 }
@@ -1233,6 +1321,8 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
       bool big = false;
       for (int q = 0; q < 4; q++) { c2.cnt[q] = t[q]; big |= t[q] > (uint32_t)kSmallMax; }
       c2.s1 = t[0] + t[1] + t[2] + t[3];
+      // the paper's chunked SPA reads the sorted records from global memory
+      if ((j.opts & OPT_BLOCKED_SPA) && c2.s1 > 0) big = true;
       if (big) c2.flags |= SF_BIG;
     }
   }

@@ -50,9 +50,9 @@ int g_na_sms[kMaxDevices] = {};
 size_t na_up(size_t v) { return (v + 255) / 256 * 256; }
 
 // Largest a1 chunk count and a2 tile count of any call: a1 chunks hold at
-// least 4096 points, a2 tiles at least cls_tile(CCH_F64) = 2048.
+// least 4096 points, a2 tiles at least kClsMinTile.
 constexpr int32_t kNaMaxChunk1 = (int32_t)((kNoAllocMaxPoints + 4095) / 4096);
-constexpr int32_t kNaMaxTile2 = (int32_t)((kNoAllocMaxPoints + 2047) / 2048);
+constexpr int32_t kNaMaxTile2 = (int32_t)((kNoAllocMaxPoints + kClsMinTile - 1) / kClsMinTile);
 
 // The one fixed layout of the array, sized for kNoAllocMaxPoints points and
 // the largest chunk and tile counts, so that every buffer -- in particular

@@ -73,11 +73,13 @@ __global__ void k_hull_pack(const int32_t* out_idx, const int64_t* offs, const i
   }
 }
 
-// Pinned host buffers by power-of-two size class, reused across requests and
-// servers (pinning memory costs far more than copying into it); freed by
-// cch_release_workspace.
-class PinnedPool {
+// Buffers by power-of-two size class, reused across requests and servers:
+// pinned host memory (pinning costs far more than copying into it) for
+// requests submitted from the host, device memory for requests submitted
+// from the device (their resident copies).  Freed by cch_release_workspace.
+class BufPool {
  public:
+  explicit BufPool(bool device) : device_(device) {}
   void* get(size_t bytes, size_t& cls) {
     cls = size_t(1) << 16;
     while (cls < bytes) cls <<= 1;
@@ -87,7 +89,8 @@ class PinnedPool {
       if (!v.empty()) { void* p = v.back(); v.pop_back(); return p; }
     }
     void* p = nullptr;
-    if (cudaMallocHost(&p, cls) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    const cudaError_t e = device_ ? cudaMalloc(&p, cls) : cudaMallocHost(&p, cls);
+    if (e != cudaSuccess) { cudaGetLastError(); return nullptr; }
     return p;
   }
   void put(void* p, size_t cls) {
@@ -98,10 +101,14 @@ class PinnedPool {
   void release() {
     std::lock_guard<std::mutex> lk(mu_);
     for (auto& kv : free_)
-      for (void* p : kv.second) cudaFreeHost(p);
+      for (void* p : kv.second) {
+        if (device_) cudaFree(p);
+        else cudaFreeHost(p);
+      }
     free_.clear();
   }
  private:
+  bool device_;
   std::mutex mu_;
   std::map<size_t, std::vector<void*>> free_;
 };
@@ -121,13 +128,15 @@ void copy_in(void* dst, const void* src, size_t bytes) {
   for (auto& t : th) t.join();
 }
 
-PinnedPool g_pinned;
+BufPool g_pinned(false);   // host copies of host-submitted requests
+BufPool g_devbuf(true);    // resident copies of device-submitted requests
 
 struct Request {
   uint64_t ticket = 0;
   int64_t n = 0;
-  void* pts = nullptr;               // pinned host copy of the input until uploaded
-  size_t pts_cls = 0;
+  void* pts = nullptr;               // copy of the input until its batch has read it: pinned
+  size_t pts_cls = 0;                // host memory, or device memory when `dev`
+  bool dev = false;
   Clock::time_point t_submit;
   int32_t status = CCH_OK;
   int32_t count = 0;
@@ -170,7 +179,10 @@ struct Slot {
 
 }  // namespace
 
-void serve_release_pinned() { g_pinned.release(); }
+void serve_release_pinned() {
+  g_pinned.release();
+  g_devbuf.release();
+}
 
 }  // namespace cch
 
@@ -193,7 +205,14 @@ struct cch_server {
   Clock::time_point t_first, t_last;
   std::vector<double> latencies;
   int64_t nfinished = 0;
-  PinnedPool& pinned = g_pinned;
+  BufPool& pinned = g_pinned;
+  std::mutex submit_mu;                      // guards submit_ev
+  cudaEvent_t submit_ev = nullptr;           // completion of a device submit's copy
+  BufPool& devbuf = g_devbuf;
+  void put_input(Request* r) {
+    (r->dev ? devbuf : pinned).put(r->pts, r->pts_cls);
+    r->pts = nullptr;
+  }
 
   size_t point_bytes() const { return cfg.dtype == CCH_F64 ? 16 : 8; }
   // device bytes a batch of `npts` points in `nsets` sets holds while it runs
@@ -210,7 +229,7 @@ struct cch_server {
 
 void cch_server::finish(Slot& sl, int status) {
   if (status != CCH_OK) cudaStreamSynchronize(sl.st);   // no copy may still read a pinned input
-  for (Request* r : sl.reqs) { pinned.put(r->pts, r->pts_cls); r->pts = nullptr; }
+  for (Request* r : sl.reqs) put_input(r);
   const Clock::time_point now = Clock::now();
   const int32_t* counts = static_cast<const int32_t*>(sl.h_counts.p);
   const int32_t* hull = static_cast<const int32_t*>(sl.h_hull.p);
@@ -259,7 +278,7 @@ void cch_server::launch(Slot& sl) {
   for (int32_t i = 0; i < nsets && st == CCH_OK; i++) {
     const Request* r = sl.reqs[i];
     if (r->n && cudaMemcpyAsync(static_cast<unsigned char*>(sl.d_pts.p) + sl.offs[i] * pb, r->pts, (size_t)r->n * pb,
-                                cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
+                                r->dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
       st = CCH_ERR_CUDA;
   }
   if (st == CCH_OK &&
@@ -291,7 +310,7 @@ void cch_server::launch(Slot& sl) {
 // Next stage of a batch whose event has completed (scheduler thread).
 void cch_server::advance(Slot& sl) {
   if (sl.stage == 1) {
-    for (Request* r : sl.reqs) { pinned.put(r->pts, r->pts_cls); r->pts = nullptr; }
+    for (Request* r : sl.reqs) put_input(r);
     const int64_t total = *static_cast<const int64_t*>(sl.h_total.p);
     if (total > 0) {
       if (!sl.h_hull.ensure(4 * (size_t)total)) { finish(sl, CCH_ERR_NOMEM); return; }
@@ -373,6 +392,7 @@ extern "C" int cch_serve_create(const cch_serve_config* cfg, cch_server** out) {
   if (!s->cfg.max_batch) s->cfg.max_batch = 4096;
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return CCH_ERR_CUDA; }
   s->slots.resize(s->cfg.num_streams);
+  if (cudaEventCreateWithFlags(&s->submit_ev, cudaEventDisableTiming) != cudaSuccess) { delete s; return CCH_ERR_CUDA; }
   for (auto& sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -380,6 +400,7 @@ extern "C" int cch_serve_create(const cch_serve_config* cfg, cch_server** out) {
         if (q.st) cudaStreamDestroy(q.st);
         if (q.ev) cudaEventDestroy(q.ev);
       }
+      cudaEventDestroy(s->submit_ev);
       delete s;
       return CCH_ERR_CUDA;
     }
@@ -389,22 +410,20 @@ extern "C" int cch_serve_create(const cch_serve_config* cfg, cch_server** out) {
   return CCH_OK;
 }
 
-extern "C" int cch_serve_submit(cch_server* srv, const void* points, int64_t n, uint64_t* ticket) {
+namespace {
+int serve_check(cch_server* srv, const void* points, int64_t n, uint64_t* ticket) {
   if (!srv || !ticket || n < 0 || (n > 0 && !points)) return CCH_ERR_INVALID;
   if (n > kMaxSetPoints) return CCH_ERR_RANGE;
   if (srv->need_of(n, 1) > srv->cfg.budget_bytes) return CCH_ERR_RANGE;
-  Request* r = new Request();
-  r->n = n;
-  if (n) {
-    const size_t bytes = (size_t)n * srv->point_bytes();
-    r->pts = srv->pinned.get(bytes, r->pts_cls);
-    if (!r->pts) { delete r; return CCH_ERR_NOMEM; }
-    copy_in(r->pts, points, bytes);
-  }
+  return CCH_OK;
+}
+
+// Queue a request whose input copy is complete.
+int serve_enqueue(cch_server* srv, Request* r, uint64_t* ticket) {
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop || srv->pending.size() >= (size_t)srv->cfg.max_pending) {
-      srv->pinned.put(r->pts, r->pts_cls);
+      srv->put_input(r);
       const int code = srv->stop ? CCH_ERR_INVALID : CCH_ERR_BUSY;
       delete r;
       return code;
@@ -417,6 +436,48 @@ extern "C" int cch_serve_submit(cch_server* srv, const void* points, int64_t n, 
   }
   srv->cv.notify_one();
   return CCH_OK;
+}
+}  // namespace
+
+extern "C" int cch_serve_submit(cch_server* srv, const void* points, int64_t n, uint64_t* ticket) {
+  int st = serve_check(srv, points, n, ticket);
+  if (st != CCH_OK) return st;
+  Request* r = new Request();
+  r->n = n;
+  if (n) {
+    const size_t bytes = (size_t)n * srv->point_bytes();
+    r->pts = srv->pinned.get(bytes, r->pts_cls);
+    if (!r->pts) { delete r; return CCH_ERR_NOMEM; }
+    copy_in(r->pts, points, bytes);
+  }
+  return serve_enqueue(srv, r, ticket);
+}
+
+extern "C" int cch_serve_submit_device(cch_server* srv, const void* points, int64_t n, void* stream,
+                                       uint64_t* ticket) {
+  int st = serve_check(srv, points, n, ticket);
+  if (st != CCH_OK) return st;
+  if ((uintptr_t)points % srv->point_bytes()) return CCH_ERR_INVALID;
+  Request* r = new Request();
+  r->n = n;
+  r->dev = true;
+  if (n) {
+    const size_t bytes = (size_t)n * srv->point_bytes();
+    r->pts = srv->devbuf.get(bytes, r->pts_cls);
+    if (!r->pts) { delete r; return CCH_ERR_NOMEM; }
+    // ordered after the caller's work on `stream`; complete before return,
+    // so the caller may reuse or free its buffer at once
+    cudaStream_t cs = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(srv->submit_mu);
+    if (cudaMemcpyAsync(r->pts, points, bytes, cudaMemcpyDeviceToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(srv->submit_ev, cs) != cudaSuccess || cudaEventSynchronize(srv->submit_ev) != cudaSuccess) {
+      cudaGetLastError();
+      srv->put_input(r);
+      delete r;
+      return CCH_ERR_CUDA;
+    }
+  }
+  return serve_enqueue(srv, r, ticket);
 }
 
 extern "C" int cch_serve_poll(cch_server* srv, cch_done* done, int max, int* n_done) {
@@ -488,8 +549,9 @@ extern "C" int cch_serve_destroy(cch_server* srv) {
     cudaEventDestroy(sl.ev);
     cudaStreamDestroy(sl.st);
   }
+  cudaEventDestroy(srv->submit_ev);
   for (auto& kv : srv->finished) delete kv.second;
-  for (Request* r : srv->pending) { srv->pinned.put(r->pts, r->pts_cls); delete r; }
+  for (Request* r : srv->pending) { srv->put_input(r); delete r; }
   delete srv;
   return CCH_OK;
 }

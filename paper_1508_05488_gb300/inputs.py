@@ -146,6 +146,39 @@ def serve_request(i: int, seed: int = 8, lo: float = 1e3, hi: float = 2e7) -> np
     return shell_f64(n, sub)
 
 
+def serve_request_meta(i: int, seed: int = 8, lo: float = 1e3, hi: float = 2e7):
+    """Size, kind and sub-seed of request i of the serving stream (the same
+    draws as serve_request)."""
+    rng = np.random.default_rng([seed, i])
+    n = int(np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+    kind = SERVE_KINDS[int(rng.integers(0, 4))]
+    sub = int(rng.integers(0, 2 ** 31))
+    return n, kind, sub
+
+
+def serve_request_device(i: int, device, seed: int = 8):
+    """Request i of the serving stream drawn directly in device memory (a
+    seeded torch generator on the device; the same size and kind as
+    serve_request, other coordinates): float64 [n, 2] uniform in the unit
+    square, the unit disk, Gaussian sigma 1, or the shell 0.99 <= r <= 1."""
+    import torch
+    n, kind, sub = serve_request_meta(i, seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(sub)
+    f64 = torch.float64
+    if kind == "square":
+        return torch.rand((n, 2), dtype=f64, device=device, generator=g)
+    if kind == "gauss":
+        return torch.randn((n, 2), dtype=f64, device=device, generator=g)
+    u = torch.rand((n, 2), dtype=f64, device=device, generator=g)
+    if kind == "disk":
+        r = torch.sqrt(u[:, 0])
+    else:
+        r = torch.sqrt(0.99 ** 2 + u[:, 0] * (1.0 - 0.99 ** 2))
+    t = 2.0 * np.pi * u[:, 1]
+    return torch.stack([r * torch.cos(t), r * torch.sin(t)], dim=1).contiguous()
+
+
 def poisson_arrivals(count: int, rate_per_s: float, seed: int = 8) -> np.ndarray:
     """Arrival times (s) of a Poisson process of the given rate."""
     rng = np.random.default_rng(seed + 77)

@@ -162,6 +162,26 @@ def test_stage_sets_match_method(kind, exact_only, prefilter):
     assert np.array_equal(st["hull"], m["hull"])
 
 
+@pytest.mark.parametrize("kind,n", [(k, n) for k in STAGE_KINDS for n in (3_000, 150_001)] +
+                         [("square", 2_500_003), ("disk", 2_500_003), ("i32", 2_500_003)])
+def test_blocked_spa_of_the_paper(kind, n):
+    """The paper's chunked GPU SPA (Sec. 2.2.2, cch_hull_stages opts bit 2):
+    its survivors equal the oracle's chunked restatement element by element,
+    contain the sequential SPA survivors, and the hull is unchanged.  Sizes
+    span regions below 1024 points (every point its own chunk) up to chunks
+    of hundreds of points."""
+    p = STAGE_KINDS[kind](n)
+    st = cch.stages(torch.from_numpy(p).to(DEV), blocked=True)
+    m = oracle.method(p)
+    want = oracle.blocked_spa(p, m=m)
+    assert st["status"] == 0
+    for r in range(4):
+        assert np.array_equal(st["r1"][r], m["r1"][r]), ("round 1", r)
+        assert np.array_equal(st["spa"][r], want[r]), ("blocked SPA", r)
+        assert np.isin(m["spa"][r], st["spa"][r]).all(), ("superset of the sequential SPA", r)
+    assert np.array_equal(st["hull"], m["hull"])
+
+
 def test_prefilter_shrinks_round1_on_uniform_sets():
     for p in (inputs.square_f64(1_000_000, 5), inputs.disk_f64(1_000_000, 6)):
         t = torch.from_numpy(p).to(DEV)

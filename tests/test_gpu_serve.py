@@ -98,3 +98,32 @@ def test_budget_admission_and_queue_limit():
     srv = cch.Server(np.float64)
     assert cch.lib().cch_serve_release(srv._h, 12345) == -9
     srv.close()
+
+
+def test_device_submitted_requests_stay_on_the_device_and_match_alone():
+    """Requests submitted from device memory (cch_serve_submit_device) --
+    mixed with host submits, the caller's buffer overwritten right after each
+    submit -- give the oracle's hull of each request."""
+    reqs = mixed_requests(1)
+    want = [oracle.hull(p) for p in reqs]
+    with cch.Server(np.float64, num_streams=3, max_batch=4) as srv:
+        tickets, scratch = [], torch.empty((2_000_000, 2), dtype=torch.float64, device="cuda")
+        for i, p in enumerate(reqs + reqs[::-1]):
+            if i % 3 == 2:
+                tickets.append(srv.submit(p))                     # host submit
+                continue
+            d = scratch[:len(p)]
+            d.copy_(torch.from_numpy(p))
+            tickets.append(srv.submit(d))                         # device submit, copied before return
+            d.fill_(float("nan"))                                 # the caller reuses its buffer at once
+        got = drain(srv, len(tickets))
+        for t, w in zip(tickets, want + want[::-1]):
+            st, h, _ = got[t]
+            assert st == 0 and np.array_equal(h, w)
+    with cch.Server(np.int32) as srv:
+        p = inputs.disk_i32(80_000, 9)
+        t = srv.submit(torch.from_numpy(p).cuda())
+        got = drain(srv, 1)
+        assert got[t][0] == 0 and np.array_equal(got[t][1], oracle.hull(p))
+        with pytest.raises(TypeError):
+            srv.submit(torch.zeros((5, 2), dtype=torch.float64, device="cuda"))   # wrong dtype

@@ -262,22 +262,68 @@ def test_fig4_worked_example():
 
 def test_blocked_spa_of_the_paper_is_a_superset():
     """Sec. 2.2.2 runs SPA in independent chunks, each restarting t at its
-    chunk's first point; that keeps every point the sequential rule keeps."""
+    chunk's first point; that keeps every point the sequential rule keeps
+    (the sequential rule also has every earlier chunk's points and the first
+    extreme to discard against)."""
     p = inputs.disk_f64(50_000, 31)
     m = oracle.method(p)
-    pl = p.tolist()
+    blocked = oracle.blocked_spa(p, m=m)
     for k in range(4):
-        s = m["sorted"][k].tolist()
-        c = 1 if k in (0, 2) else 0
-        worse = (lambda v, t: v > t) if k in (0, 3) else (lambda v, t: v < t)
-        blocked = set()
-        for lo in range(0, len(s), 37):
-            t = pl[s[lo]][c]
-            for i in s[lo:lo + 37]:
-                if not worse(pl[i][c], t):
-                    t = pl[i][c]
-                    blocked.add(i)
-        assert set(m["spa"][k].tolist()) <= blocked
+        assert set(m["spa"][k].tolist()) <= set(blocked[k].tolist())
+        assert len(blocked[k]) < len(m["sorted"][k])        # 1024 chunks of ~10 points still discard
+
+
+def _blocked_by_dominance(p, sorted_k, k, nchunks):
+    """Brute-force definition of the chunked rule: a point is kept iff no
+    earlier point of its chunk has a strictly better compared coordinate
+    (Fig. 2 / Fig. 3: R1 smaller y, R2 larger x, R3 larger y, R4 smaller x)."""
+    c = 1 if k in (0, 2) else 0
+    better = (lambda q, r: q < r) if k in (0, 3) else (lambda q, r: q > r)
+    n = len(sorted_k)
+    L = (n + nchunks - 1) // nchunks if n else 1
+    keep = []
+    for pos, i in enumerate(sorted_k):
+        lo = pos // L * L
+        if not any(better(p[sorted_k[e]][c], p[i][c]) for e in range(lo, pos)):
+            keep.append(int(i))
+    return keep
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_blocked_spa_equals_its_dominance_definition(seed):
+    """The oracle's chunked running minimum equals the pairwise definition on
+    small sets with duplicates, ties and negative zeros, for several chunk
+    counts (one chunk, a few, one point per chunk)."""
+    rng = np.random.default_rng(900 + seed)
+    if seed % 3 == 0:
+        p = rng.integers(-6, 7, (300, 2)).astype(np.int32)
+    elif seed % 3 == 1:
+        p = (rng.integers(-8, 9, (300, 2)) / 4.0).astype(np.float64)
+        p[rng.random(300) < 0.1] *= -0.0                      # zeros of both signs among them
+    else:
+        p = inputs.disk_f64(400, 900 + seed)
+    m = oracle.method(p)
+    pl = p.tolist()
+    for nchunks in (1, 3, 7, 1024):
+        got = oracle.blocked_spa(p, nchunks=nchunks, m=m)
+        for k in range(4):
+            assert got[k].tolist() == _blocked_by_dominance(pl, m["sorted"][k].tolist(), k, nchunks), (nchunks, k)
+
+
+def test_blocked_spa_closed_forms():
+    """With at least as many chunks as points every region point is its own
+    chunk and is kept; the hull of the extremes and the kept points is the
+    hull of the set."""
+    p = inputs.square_f64(3000, 32)
+    m = oracle.method(p)
+    allk = oracle.blocked_spa(p, nchunks=10 ** 6, m=m)
+    for k in range(4):
+        assert np.array_equal(allk[k], m["sorted"][k])
+    for nchunks in (1, 5, 1024):
+        b = oracle.blocked_spa(p, nchunks=nchunks, m=m)
+        keep = np.unique(np.concatenate([m["ext"]] + b))
+        sub = oracle.hull(p[keep])
+        assert np.array_equal(np.sort(keep[sub]), np.sort(oracle.hull(p)))
 
 
 # ------------------------------------------------ multi-core CPU baseline
