@@ -248,13 +248,30 @@ def batched_bench(cch, torch, dev, stream, nsets):
                 break
     reps = 5
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def time_batched():
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            batched()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_default = time_batched()
+    # the run-time choices tuned on this batch (outside the timed region),
+    # then the same measurement with them
+    tuned = cch.autotune_batched(d, off, idx_b, cnt_b, reps=2, stream=stream)
+    batched()
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        batched()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / reps
+    same_tuned = bool(torch.equal(cnt_b, cnt_c))
+    if same_tuned:
+        for s_ in range(nsets):
+            c = int(cnt_b[s_])
+            if c > 0 and not torch.equal(idx_b[offs[s_]:offs[s_] + c], idx_c[offs[s_]:offs[s_] + c]):
+                same_tuned = False
+                break
+    ms_batch = time_batched()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsets)]
     torch.cuda.synchronize()
     e0.record(stream)
@@ -264,8 +281,13 @@ def batched_bench(cch, torch, dev, stream, nsets):
     ms_calls = e0.elapsed_time(e1)
     lat = sorted(a.elapsed_time(b) for a, b in ev)
     q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+    hbm, _ = peaks()
     return {"config": f"{nsets} int32 sets, sizes log-uniform in [256, 2^20] (seed 7), square or disk",
             "points": n_tot, "hulls_per_s": nsets / (ms_batch * 1e-3), "ms_per_batch": ms_batch,
+            "hbm_frac": 2 * 8 * n_tot / (ms_batch * 1e-3) / 1e9 / hbm,
+            "hbm_frac_note": "two reads of every 8-byte point over the batch time, against the measured copy bandwidth",
+            "default_choices_ms_per_batch": ms_default, "tuned_choices": tuned,
+            "identical_with_tuned_choices": same_tuned,
             "per_call_hulls_per_s": nsets / (ms_calls * 1e-3), "per_call_ms_total": ms_calls,
             "per_call_p50_ms": q(0.50), "per_call_p99_ms": q(0.99),
             "speedup_vs_per_call": ms_calls / ms_batch, "identical_to_per_call": same}
@@ -491,6 +513,65 @@ def survivors(kinds, sizes, reps):
     return rows
 
 
+def profile_run(args):
+    """Warm-up calls, then `--steps` calls of one workload (for ncu launch
+    lists and captures): the batched 4096-set call or one extra configuration."""
+    import torch
+    import paper_1508_05488_gb300 as cch
+    from paper_1508_05488_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    if args.profile == "h2d":
+        # pinned host -> device copy bandwidth with 1, 2, 4 and 8 streams
+        # (the floor under the end-to-end number: the step's inputs cross it)
+        nbytes = 320_000_000
+        out = {}
+        for ns in (1, 2, 4, 8):
+            hs = [torch.empty(nbytes // ns, dtype=torch.uint8).pin_memory() for _ in range(ns)]
+            ds = [torch.empty(nbytes // ns, dtype=torch.uint8, device=dev) for _ in range(ns)]
+            sts = [torch.cuda.Stream(device=dev) for _ in range(ns)]
+            for _ in range(2):
+                for h, d_, st in zip(hs, ds, sts):
+                    with torch.cuda.stream(st):
+                        d_.copy_(h, non_blocking=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                for h, d_, st in zip(hs, ds, sts):
+                    with torch.cuda.stream(st):
+                        d_.copy_(h, non_blocking=True)
+            torch.cuda.synchronize()
+            out[ns] = nbytes * args.steps / (time.perf_counter() - t0) / 1e9
+        print(json.dumps({"profile": "h2d", "bytes_per_copy_round": nbytes, "rounds": args.steps,
+                          "gb_per_s_by_streams": out}))
+        return 0
+    if args.profile == "batched":
+        pts, off = inputs.batched_i32(args.batched_sets, seed=7)
+        d = torch.from_numpy(pts).to(dev)
+        n = int(off[-1])
+        idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        cnt = torch.empty(args.batched_sets, dtype=torch.int32, device=dev)
+        call = lambda: cch.hull_batched_async(d, off, idx, cnt)
+    else:
+        cfg = {c[0]: c for c in EXTRA_CONFIGS}[args.profile]
+        seed = {"degenerate_f64": 5, "circle_f64": 6, "square_i32": 1}[cfg[1]]
+        d = torch.from_numpy(getattr(inputs, cfg[1])(cfg[2], seed)).to(dev)
+        idx = torch.empty(cfg[2], dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        call = lambda: cch.hull_async(d, idx, cnt)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "calls": args.steps, "ms_per_call": e0.elapsed_time(e1) / args.steps,
+                      "count0": int(cnt[0])}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,6 +590,10 @@ def main():
     ap.add_argument("--batched-sets", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered load (0: skip the serving measurement)")
+    ap.add_argument("--profile", default=None,
+                    help="profiling run: `batched` (the 4096-set call), `h2d` (pinned copy bandwidth) or a configuration name "
+                         "(degenerate_20M, circle_2M, int32_1M): warm-up calls, then --steps calls, "
+                         "one summary line, nothing else")
     ap.add_argument("--kinds", default=",".join(KINDS),
                     help="comma-separated subset of square,disk,gauss (profiling runs)")
     args = ap.parse_args()
@@ -518,6 +603,8 @@ def main():
         return run_reference(args)
     kinds = tuple(k for k in args.kinds.split(",") if k)
     assert kinds and all(k in KINDS for k in kinds), kinds
+    if args.profile:
+        return profile_run(args)
     if args.survivors:
         print(json.dumps({"survivors": survivors(kinds, SURVIVOR_SIZES, max(args.steps, 1)), "unit_time": "us",
                           "dtype": "f64", "data": "synthetic"}))

@@ -137,17 +137,26 @@ int cch_hull_f32soa(const float *x, const float *y, int64_t n, int32_t *out_idx,
  *                 Fig. 2's rule restarted at its chunk's first point) gives
  *                 spa_idx and its counts, on the paper's round-1 sets (bit 2
  *                 implies bit 1; the hull still comes from the sequential
- *                 rule, so out_idx is unchanged); other bits must be 0
+ *                 rule, so out_idx is unchanged); bit 3: round 1 discards
+ *                 the points strictly inside the octagon of the four
+ *                 extremes and four diagonal extremes (Akl-Toussaint, the
+ *                 paper's reference [17]; D_r, the point with the smallest
+ *                 FP32 score X+Y, Y-X, -X-Y, X-Y of its coordinates' views,
+ *                 ties to the smallest index, between E_r and E_{r+1} when
+ *                 it lies strictly outside that quadrilateral edge), instead
+ *                 of the quadrilateral alone; implies bit 1; other bits
+ *                 must be 0
  *   r1_idx        device int32[max(n,1)]: round-1 survivors (Sec. 2.1.1),
  *                 region after region, index order within a region
  *   r1_region     device int32[max(n,1)]: their regions 1..4
  *   spa_idx       device int32[max(n,1)]: SPA survivors (Fig. 2) of R1..R4
  *                 in sorted (Table 1) order, region after region
- *   counts_host   host int64[11]: s1, records of R1..R4, survivors of R1..R4,
- *                 the device status (0 or a negative code), and the number of
+ *   counts_host   host int64[16]: s1, records of R1..R4, survivors of R1..R4,
+ *                 the device status (0 or a negative code), the number of
  *                 LSD radix passes the multi-block sort ran (0 when the set
  *                 took the shared-memory path; byte passes whose digit is the
- *                 same for every record are skipped)
+ *                 same for every record are skipped), with bit 3 the indices
+ *                 of D_1..D_4 (-1 where unused; otherwise -1), and 0
  *   out_idx, out_count   as for cch_hull
  * Synchronises the stream before returning.
  */
@@ -206,6 +215,50 @@ int cch_selftest_wait(int32_t *status_dev, void *stream);
  */
 int cch_hull_noalloc(const void *points, int64_t n, int dtype,
                      int32_t *out_idx, int32_t *out_count, void *stream);
+
+/* ------------------------------------------------------------- tuning --
+ * Run-time choices of a call, none of which changes a result: the largest
+ * region sorted in shared memory (above it the multi-block sort runs), the
+ * sample behind the dominance prefilter (m = min(n, stair_max, max(stair_min,
+ * n / stair_div))), the smallest a1 chunk, and a2's CTAs per SM.  A table
+ * keyed by GPU (name, SM count), dtype, single set or batch, and size bucket
+ * (floor(log2(points per set)), cch_tune_bucket) holds them; calls without
+ * an entry use the defaults.  The table can be filled by hand, by
+ * cch_autotune_batched, or from a JSON cache file. */
+typedef struct cch_tune_params {
+  int32_t small_max;     /* 1 .. 16384 */
+  int32_t stair_div;     /* >= 1 */
+  int32_t stair_min;     /* 1 .. stair_max */
+  int32_t stair_max;     /* <= 2^24 */
+  int32_t a1_len_min;    /* 4096 .. 2^26, a multiple of 1024 */
+  int32_t cls_per_sm;    /* 1 or 2 */
+} cch_tune_params;
+
+/* Size bucket of a call of npts points in nsets sets. */
+int cch_tune_bucket(int64_t npts, int32_t nsets);
+/* Set / get the entry of (gpu, sms, dtype, batched 0/1, bucket); gpu NULL
+ * means the current device (sms ignored).  Set returns CCH_ERR_INVALID for
+ * values outside the ranges above.  Get fills *p with the entry, or with the
+ * defaults and returns CCH_ERR_NOTFOUND. */
+int cch_tune_set(const char *gpu, int32_t sms, int32_t dtype, int32_t batched, int32_t bucket,
+                 const cch_tune_params *p);
+int cch_tune_get(const char *gpu, int32_t sms, int32_t dtype, int32_t batched, int32_t bucket,
+                 cch_tune_params *p);
+/* Forget every entry. */
+int cch_tune_clear(void);
+/* Write the table to a JSON file; merge a file written by cch_tune_save into
+ * it (the whole file is checked first: CCH_ERR_INVALID leaves the table
+ * unchanged, CCH_ERR_NOTFOUND if the file cannot be opened). */
+int cch_tune_save(const char *path);
+int cch_tune_load(const char *path);
+/* Measure the choices on this batch (same arguments as cch_hull_batched;
+ * device buffers, synchronises the stream): coordinate descent over
+ * candidate values of each choice, `reps` timed calls per candidate; the
+ * fastest goes into the table under this batch's key and into *best (if not
+ * NULL).  The outputs hold the batch's hulls afterwards. */
+int cch_autotune_batched(const void *points, const int64_t *offsets, int32_t nsets, int32_t dtype,
+                         int32_t *out_idx, int32_t *out_counts, void *stream, int32_t reps,
+                         cch_tune_params *best);
 
 /* Bytes of device scratch one cch_hull call of this size uses. */
 size_t cch_workspace_bytes(int64_t n, int dtype);

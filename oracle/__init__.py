@@ -17,6 +17,10 @@ Contents
   * ``blocked_spa(points)`` -- the SPA of the paper's GPU implementation
     (Sec. 2.2.2): each region's sorted points in 1024 consecutive chunks,
     Fig. 2's rule restarted at every chunk's first point.
+  * ``diag_extremes(points)``, ``octagon_round1(points, diag)`` -- round 1
+    with the Akl-Toussaint octagon (the paper's reference [17]) in place of
+    the quadrilateral: the four diagonal extremes and the round-1 / SPA sets
+    without the points strictly inside the octagon.
   * ``parallel_hull(points)`` -- the multi-core CPU baseline the benchmark
     times beside the oracle (OpenMP: octagon filter, parallel merge sort,
     Andrew's chain; ``cch_cpu_parallel.c`` includes the oracle's source for
@@ -261,4 +265,95 @@ def blocked_spa(points, nchunks: int = 1024, m: dict | None = None) -> list:
             excl = np.concatenate(([c[0]], run[:-1]))     # the first point is its own start value
             keep[lo:lo + L] = c <= excl
         out.append(s[keep].astype(np.int32))
+    return out
+
+
+# ------------------------------------------- round 1 with the octagon
+
+def _f32_views(p):
+    """FP32 views of the coordinates, as the octagon mode defines them:
+    float64 with the significand truncated to 24 bits (exponent rebiased;
+    magnitudes below 2^-126 become zero of their sign), int32 rounded to the
+    nearest float.  Written from the IEEE 754 encodings with integer numpy
+    operations (float64 values of magnitude below 2^128)."""
+    if p.dtype == np.int32:
+        return p.astype(np.float32)
+    b = np.ascontiguousarray(p, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.int64)
+    lo = (b & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    sign = hi & 0x80000000
+    t = (hi & 0x7FFFFFFF) - 0x38000000
+    mag = ((t << 3) | (lo >> 29)) & 0x7FFFFFFF
+    bits = np.where(t < 0, sign, sign | mag).astype(np.uint32)
+    return bits.view(np.float32)
+
+
+def diag_extremes(points) -> np.ndarray:
+    """The diagonal extremes of the octagon mode: per direction the point with
+    the smallest FP32 score of its views -- D1 X+Y, D2 Y-X, D3 -(X+Y), D4 X-Y
+    (each a single IEEE float32 operation, -0 ordered before +0 as the
+    order words do) -- ties to the smallest index.  int32[4]; empty set: -1."""
+    p, _ = _prep(points)
+    if p.shape[0] == 0:
+        return np.full(4, -1, dtype=np.int32)
+    v = _f32_views(p)
+    X, Y = v[:, 0], v[:, 1]
+    with np.errstate(all="ignore"):
+        scores = [X + Y, Y - X, -(X + Y), X - Y]
+    out = np.zeros(4, dtype=np.int32)
+    for k, sc in enumerate(scores):
+        u = sc.astype(np.float32).view(np.uint32).astype(np.int64)
+        order = np.where(u & 0x80000000, (~u) & 0xFFFFFFFF, u | 0x80000000)   # IEEE order of the bits
+        out[k] = int(np.lexsort((np.arange(len(order)), order))[0])
+    return out
+
+
+def octagon_round1(points, diag, m: dict | None = None) -> dict:
+    """Round 1 with the octagon: vertices E1 D1 E2 D2 E3 D3 E4 D4, where
+    diag[r] is D_r's index (-1: none, the vertex is then E_{r+1}).  A point
+    strictly inside the octagon (strictly left of every edge of nonzero
+    length, exact orientation) is discarded.  Returns ``r1`` and ``spa``:
+    ``method``'s sets without those points (a point strictly inside cannot
+    beat, in its region's SPA order, a point that is not, so the SPA
+    survivors of the reduced sets are the paper's survivors outside the
+    octagon), and the vertex list ``verts``."""
+    p, _ = _prep(points)
+    if m is None:
+        m = method(points)
+    E = [int(i) for i in m["ext"]]
+    verts = []
+    for r in range(4):
+        verts.append(E[r])
+        verts.append(int(diag[r]) if diag[r] >= 0 else E[(r + 1) % 4])
+    pl = p.tolist()
+    edges = [(pl[verts[k]], pl[verts[(k + 1) % 8]]) for k in range(8)]
+    edges = [(a, b) for a, b in edges if a != b]
+
+    def inside(i):
+        q = pl[i]
+        return all(orient(a, b, q, p.dtype) > 0 for a, b in edges)
+
+    def keep(arr):
+        return np.array([i for i in arr.tolist() if not inside(i)], dtype=np.int32)
+
+    return {"r1": [keep(a) for a in m["r1"]], "spa": [keep(a) for a in m["spa"]], "verts": verts}
+
+
+def octagon_diag(points, m: dict | None = None) -> np.ndarray:
+    """The diagonal extremes the octagon mode uses: D_r of ``diag_extremes``
+    when it lies strictly outside the quadrilateral edge E_r -> E_{r+1} (and
+    that edge has nonzero length), else -1."""
+    p, _ = _prep(points)
+    if m is None:
+        m = method(points)
+    if p.shape[0] == 0:
+        return np.full(4, -1, dtype=np.int32)
+    d = diag_extremes(points)
+    E = [int(i) for i in m["ext"]]
+    pl = p.tolist()
+    out = np.full(4, -1, dtype=np.int32)
+    for r in range(4):
+        a, b = pl[E[r]], pl[E[(r + 1) % 4]]
+        if a != b and orient(a, b, pl[int(d[r])], p.dtype) < 0:
+            out[r] = d[r]
     return out

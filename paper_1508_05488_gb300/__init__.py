@@ -35,6 +35,15 @@ class ServeConfig(ctypes.Structure):
                 ("max_pending", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("dtype", ctypes.c_int32)]
 
 
+class TuneParams(ctypes.Structure):
+    """cch_tune_params."""
+    _fields_ = [("small_max", ctypes.c_int32), ("stair_div", ctypes.c_int32), ("stair_min", ctypes.c_int32),
+                ("stair_max", ctypes.c_int32), ("a1_len_min", ctypes.c_int32), ("cls_per_sm", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class Done(ctypes.Structure):
     """cch_done."""
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("count", ctypes.c_int32),
@@ -85,6 +94,19 @@ def _load():
         lib.cch_launch_count.argtypes = []
         lib.cch_selftest_wait.restype = ctypes.c_int
         lib.cch_selftest_wait.argtypes = [vp, vp]
+        tp = ctypes.POINTER(TuneParams)
+        lib.cch_tune_bucket.restype = ctypes.c_int
+        lib.cch_tune_bucket.argtypes = [i64, i32]
+        for name in ("cch_tune_set", "cch_tune_get"):
+            getattr(lib, name).restype = ctypes.c_int
+            getattr(lib, name).argtypes = [ctypes.c_char_p, i32, i32, i32, i32, tp]
+        lib.cch_tune_clear.restype = ctypes.c_int
+        lib.cch_tune_clear.argtypes = []
+        for name in ("cch_tune_save", "cch_tune_load"):
+            getattr(lib, name).restype = ctypes.c_int
+            getattr(lib, name).argtypes = [ctypes.c_char_p]
+        lib.cch_autotune_batched.restype = ctypes.c_int
+        lib.cch_autotune_batched.argtypes = [vp, vp, i32, i32, vp, vp, vp, i32, tp]
         for name in ("cch_serve_create", "cch_serve_submit", "cch_serve_poll", "cch_serve_release",
                      "cch_serve_stats", "cch_serve_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -256,7 +278,7 @@ def hull_host_ptr(host_ptr: int, n: int, dtype_code: int, out_idx_ptr: int, out_
 
 
 def stages(points, exact_only: bool = False, prefilter: bool = True, blocked: bool = False,
-           stream=None) -> dict:
+           octagon: bool = False, stream=None) -> dict:
     """Run one hull and return its intermediate sets (synchronises).
 
     exact_only  every float64 quadrilateral test in exact arithmetic (no FP32 filter)
@@ -266,10 +288,14 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, blocked: bo
                 chunks per region, each restarting at its first point) on the
                 paper's round-1 sets (implies prefilter=False); the hull is
                 the same
+    octagon     round 1 discards the points strictly inside the octagon of the
+                four extremes and the four diagonal extremes (implies
+                prefilter=False); ``diag`` holds the diagonal extremes used
+                (-1 where none)
 
     ``r1`` list of 4 int32 arrays (round-1 survivors per region, index order),
     ``spa`` list of 4 int32 arrays (SPA survivors per region, sorted order),
-    ``hull`` int32 array, ``counts`` int64[11], ``status``, ``passes`` (radix
+    ``hull`` int32 array, ``counts`` int64[16], ``status``, ``passes`` (radix
     passes of the multi-block sort, 0 on the shared-memory path)."""
     import torch
     _check_points(points)
@@ -281,9 +307,10 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, blocked: bo
     spa = torch.empty(m, dtype=torch.int32, device=dev)
     out_idx = torch.empty(m, dtype=torch.int32, device=dev)
     out_count = torch.empty(1, dtype=torch.int32, device=dev)
-    counts = np.zeros(11, dtype=np.int64)
+    counts = np.zeros(16, dtype=np.int64)
     rc = _load().cch_hull_stages(points.data_ptr() if n else None, n, _dtype_code(points),
-                                 (1 if exact_only else 0) | (0 if prefilter else 2) | (4 if blocked else 0),
+                                 (1 if exact_only else 0) | (0 if prefilter else 2) | (4 if blocked else 0)
+                                 | (8 if octagon else 0),
                                  r1.data_ptr(), r1r.data_ptr(),
                                  spa.data_ptr(), counts.ctypes.data, out_idx.data_ptr(),
                                  out_count.data_ptr(), _stream_handle(stream))
@@ -307,6 +334,7 @@ def stages(points, exact_only: bool = False, prefilter: bool = True, blocked: bo
         "counts": counts,
         "status": int(counts[9]),
         "passes": int(counts[10]),
+        "diag": counts[11:15].copy(),
     }
 
 
@@ -334,6 +362,40 @@ def profile_read() -> tuple[dict, int]:
     if k < 0:
         raise CchError(k, "cch_profile_read")
     return {STAGE_NAMES[i]: float(ms[i]) for i in range(k)}, int(calls[0])
+
+
+def tune_set(params: dict, dtype_code: int, batched: bool, bucket: int, gpu: str | None = None, sms: int = 0):
+    """Table entry of (gpu, sms, dtype, batched, bucket); gpu None = the current device."""
+    p = TuneParams(**params)
+    _check(_load().cch_tune_set(gpu.encode() if gpu else None, sms, dtype_code, int(batched), bucket,
+                                ctypes.byref(p)), "cch_tune_set")
+
+
+def tune_get(dtype_code: int, batched: bool, bucket: int, gpu: str | None = None, sms: int = 0):
+    """(params dict, found) for the key; the defaults when there is no entry."""
+    p = TuneParams()
+    rc = _load().cch_tune_get(gpu.encode() if gpu else None, sms, dtype_code, int(batched), bucket, ctypes.byref(p))
+    if rc not in (0, -9):
+        raise CchError(rc, "cch_tune_get")
+    return p.as_dict(), rc == 0
+
+
+def autotune_batched(points, offsets, out_idx=None, out_counts=None, reps: int = 3, stream=None) -> dict:
+    """Measure the run-time choices on this batch and keep the fastest for its key."""
+    import torch
+    _check_points(points)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nsets = off.shape[0] - 1
+    n = int(off[-1])
+    if out_idx is None:
+        out_idx = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    if out_counts is None:
+        out_counts = torch.empty(max(nsets, 1), dtype=torch.int32, device=points.device)
+    best = TuneParams()
+    _check(_load().cch_autotune_batched(points.data_ptr() if n else None, off.ctypes.data, nsets, _dtype_code(points),
+                                        out_idx.data_ptr(), out_counts.data_ptr(), _stream_handle(stream), reps,
+                                        ctypes.byref(best)), "cch_autotune_batched")
+    return best.as_dict()
 
 
 def launch_count() -> int:

@@ -220,7 +220,7 @@ int run(Job& j, const std::vector<SetDesc>* sets_host, cudaStream_t stream, Stag
     j.sets = dsets;
   }
   if (stages) { j.r1_idx = stages->r1_idx; j.r1_region = stages->r1_region; }
-  Launch La{stream, grid_cap(), 2 * sm_count()};
+  Launch La{stream, grid_cap(), j.tune.cls_per_sm * sm_count()};
   ProfRec rec{};
   cudaEvent_t* ev = prof_begin(rec);
   int nk = 0;
@@ -274,15 +274,16 @@ Job single_job(const void* points, int64_t n, int dtype, int32_t* out_idx, int32
   j.nsets = 1;
   j.dtype = dtype;
   j.opts = opts;
+  j.tune = tune_for(dtype, n, 1);
   int target = a1_target(dtype);
   int64_t len = (n + target - 1) / std::max(target, 1);
-  len = std::max<int64_t>(4096, (len + 1023) / 1024 * 1024);
+  len = std::max<int64_t>(j.tune.a1_len_min, (len + 1023) / 1024 * 1024);
   j.chunk1_len = len;
   int32_t nch = (int32_t)((n + len - 1) / len);
   j.nchunk1 = nch;
   const int ct = cls_tile(dtype);
   j.ntile2 = (int32_t)((n + ct - 1) / ct);
-  j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
+  j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n, j.tune) + kStairChunk - 1) / kStairChunk) : 0;
   j.nchunkP = (j.ntile2 + kPlanTiles - 1) / kPlanTiles;
   j.sets = nullptr;
   j.one = SetDesc{0, n, 0, nch, 0, j.ntile2, 0, j.nchunk3, 0, j.nchunkP};
@@ -378,8 +379,9 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
   if (N > 0 && !points) return CCH_ERR_INVALID;
   if ((uintptr_t)points % (dtype == CCH_F64 ? 16 : 8)) return CCH_ERR_INVALID;
   std::vector<SetDesc> sets(nsets);
+  const Tune tune = tune_for(dtype, N, nsets);
   int target = a1_target(dtype);
-  int64_t len = std::max<int64_t>(16384, ((N + target - 1) / std::max(target, 1) + 1023) / 1024 * 1024);
+  int64_t len = std::max<int64_t>(tune.a1_len_min, ((N + target - 1) / std::max(target, 1) + 1023) / 1024 * 1024);
   int64_t nch = 0, nt = 0, n3 = 0, np_ = 0;
   const int ct = cls_tile(dtype);
   for (int32_t s = 0; s < nsets; s++) {
@@ -388,7 +390,7 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
     if (n > kMaxSetPoints) return CCH_ERR_RANGE;
     int32_t c = (int32_t)((n + len - 1) / len);
     int32_t t = (int32_t)((n + ct - 1) / ct);
-    int32_t c3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
+    int32_t c3 = n > 0 ? (int32_t)((stairs_sample(n, tune) + kStairChunk - 1) / kStairChunk) : 0;
     int32_t cp = (t + kPlanTiles - 1) / kPlanTiles;
     sets[s] = SetDesc{offsets[s], n, (int32_t)nch, c, (int32_t)nt, t, (int32_t)n3, c3, (int32_t)np_, cp};
     nch += c;
@@ -401,6 +403,7 @@ int cch_hull_batched(const void* points, const int64_t* offsets, int32_t nsets, 
   j.N = N;
   j.nsets = nsets;
   j.dtype = dtype;
+  j.tune = tune;
   j.nchunk1 = (int32_t)nch;
   j.ntile2 = (int32_t)nt;
   j.nchunk3 = (int32_t)n3;
@@ -498,8 +501,8 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   int st = check_common(points, n, dtype, out_idx, out_count);
   if (st != CCH_OK) return st;
   if (!r1_idx || !r1_region || !spa_idx || !counts_host) return CCH_ERR_INVALID;
-  if (opts & ~(uint32_t)(OPT_NO_FILTER | OPT_NO_PREFILTER | OPT_BLOCKED_SPA)) return CCH_ERR_INVALID;
-  if (opts & OPT_BLOCKED_SPA) opts |= OPT_NO_PREFILTER;   // the paper's round-1 sets
+  if (opts & ~(uint32_t)(OPT_NO_FILTER | OPT_NO_PREFILTER | OPT_BLOCKED_SPA | OPT_OCTAGON)) return CCH_ERR_INVALID;
+  if (opts & (OPT_BLOCKED_SPA | OPT_OCTAGON)) opts |= OPT_NO_PREFILTER;   // the paper's round 1 (or its octagon form)
   Job j = single_job(points, n, dtype, out_idx, out_count, opts);
   StageOut so{r1_idx, r1_region, spa_idx};
   Workspace* ws = nullptr;
@@ -517,6 +520,8 @@ int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int
   for (int r = 0; r < 4; r++) counts_host[5 + r] = (opts & OPT_BLOCKED_SPA) ? c.sb[r] : c.s2[r];
   counts_host[9] = c.status != 0 ? c.status : (int32_t)ctr[CT_ERR];
   counts_host[10] = c.passes;
+  for (int r = 0; r < 4; r++) counts_host[11 + r] = (opts & OPT_OCTAGON) ? c.didx[r] : -1;
+  counts_host[15] = 0;
   return CCH_OK;
 }
 

@@ -62,12 +62,22 @@ constexpr int kPlanTiles = 64;         // a2 tiles per survivor-count chunk (one
 // set's tail) and when a2 starts (a2 hands out its tiles from the last to the
 // first).
 constexpr int64_t kL2KeepBytes = int64_t(48) << 20;
-// Sample of a set: its last m points (the most recently streamed by a1),
-// m = min(n, 2^20, max(8192, n / 16)).
-__host__ __device__ inline int64_t stairs_sample(int64_t n) {
-  int64_t m = n / 16;
-  if (m < kStairMin) m = kStairMin;
-  if (m > kStairSample) m = kStairSample;
+// Run-time choices of a call.  None of them changes a result (each only
+// moves work between equivalent paths or resizes a sample that feeds an
+// exact prefilter); the tuner (tune.cu) picks them per size bucket.
+struct Tune {
+  int32_t small_max;    // largest region of the shared-memory sort path (1 .. kSmallMax)
+  int32_t stair_div;    // stairs sample m = min(n, stair_max, max(stair_min, n / stair_div))
+  int32_t stair_min;
+  int32_t stair_max;
+  int32_t a1_len_min;   // smallest a1 chunk in points (a multiple of 1024)
+  int32_t cls_per_sm;   // a2 CTAs per SM (1 or 2)
+};
+// Sample of a set: its last m points (the most recently streamed by a1).
+__host__ __device__ inline int64_t stairs_sample(int64_t n, const Tune& t) {
+  int64_t m = n / t.stair_div;
+  if (m < t.stair_min) m = t.stair_min;
+  if (m > t.stair_max) m = t.stair_max;
   return m < n ? m : n;
 }
 constexpr int kSortItems = 16;
@@ -76,6 +86,8 @@ constexpr int kSortPasses = 9;         // 8 key bytes + the region digit
 // A set whose four regions each hold at most kSmallMax round-1 survivors is
 // sorted and SPA-scanned by one CTA per region in shared memory.
 constexpr int kSmallMax = 16384;
+// kStairMin / kStairSample: the default sample is min(n, 2^20, max(8192, n / 16))
+constexpr Tune kTuneDefault{kSmallMax, 16, (int32_t)kStairMin, (int32_t)kStairSample, 4096, 2};
 constexpr int kSpaItems = 8;
 constexpr int kSpaTile = kThreads * kSpaItems;      // 2048 records
 constexpr int kChainItems = 16;
@@ -141,6 +153,7 @@ struct Job {
   int64_t chunk1_len;   // a1 chunk length (points), multiple of 256
   uint32_t epoch;       // look-back flag epoch of this call (1..0xFFFF)
   uint32_t opts;        // OPT_* bits
+  Tune tune;            // run-time choices (the same results with any valid choice)
   const SetDesc* sets;  // device array, or nullptr -> use `one`
   SetDesc one;
   int32_t* out_idx;     // device
@@ -153,6 +166,7 @@ enum : uint32_t {
   OPT_NO_FILTER = 1u,     // force the exact path for every f64 quadrilateral test
   OPT_NO_PREFILTER = 2u,  // keep every round-1 survivor (the paper's round 1 as printed)
   OPT_BLOCKED_SPA = 4u,   // stage output: the paper's chunked GPU SPA (Sec. 2.2.2); implies OPT_NO_PREFILTER
+  OPT_OCTAGON = 8u,       // round 1 discards inside the extremes' octagon (Akl-Toussaint); implies OPT_NO_PREFILTER
 };
 
 __device__ __forceinline__ SetDesc get_set(const Job& j, int s) {
@@ -165,6 +179,7 @@ struct Part {
   uint32_t idx[4];
   uint32_t bad;          // smallest top-word magnitude of a nonzero coordinate (float64)
   uint32_t lomag;        // the same over every coordinate, zeros included
+  uint64_t dq[4];        // OPT_OCTAGON: diagonal extremes, order word of the FP32 score << 32 | index
 };
 
 // Device-resident per-set state (zeroed every call).
@@ -188,6 +203,11 @@ struct SetCtl {
   uint32_t arrive5;          // SF_LOCALOUT: chain blocks done
   uint32_t nal[4];           // SF_LOCALOUT: output points of chain r (its kept positions but the last)
   uint32_t sb[4];            // OPT_BLOCKED_SPA: points the chunked SPA keeps per region
+  // OPT_OCTAGON: vertices E1 D1 E2 D2 E3 D3 E4 D4 (D_r = E_{r+1} where the diagonal
+  // extreme adds nothing) and the FP32 filter of their eight edges
+  int32_t  didx[4];           // set-local index of D_r, -1 where unused
+  double   ovx[8], ovy[8];
+  float    oA[8], oB[8], oC[8], oE[8];
 };
 
 // SPA prefix-minimum look-back status of one tile: value words published
@@ -355,11 +375,82 @@ static __device__ __noinline__ int orient_f64_exact_tail(double ax, double ay, d
   return 0;
 }
 
-// FP64 filter with Shewchuk's bound (3 + 16 eps) eps (|l| + |r|), eps = 2^-53,
-// then the exact evaluation.  Valid for coordinates that are 0 or of
-// magnitude in [2^-400, 2^400] (no underflow or overflow anywhere).
+// Exact difference of two float64 values (0, or normal) as an integer times a
+// power of two: v = q * 2^e.  A nonzero value is m * 2^(E - 1075) with its
+// 53-bit significand m and biased exponent E; both operands are brought to
+// the smaller exponent, which needs a left shift of the other significand by
+// the exponent gap.  Returns false when the gap exceeds 9 bits (then the
+// shifted significands could reach 2^63 and their difference overflow).
+__device__ __forceinline__ bool diff_as_int(double a, double b, long long& q, int& e) {
+  const uint64_t ba = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
+  const bool za = (ba << 1) == 0, zb = (bb << 1) == 0;
+  const int ea = (int)((ba >> 52) & 0x7FF), eb = (int)((bb >> 52) & 0x7FF);
+  const long long ma = (long long)((ba & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const long long mb = (long long)((bb & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const long long sa = (ba >> 63) ? -ma : ma, sb = (bb >> 63) ? -mb : mb;
+  if (za && zb) { q = 0; e = 0; return true; }
+  if (za) { q = -sb; e = eb; return true; }
+  if (zb) { q = sa; e = ea; return true; }
+  const int emin = ea < eb ? ea : eb;
+  const int ga = ea - emin, gb = eb - emin;
+  if (ga > 9 || gb > 9) return false;
+  q = sa * (1ll << ga) - sb * (1ll << gb);     // |q| < 2 * 2^62
+  e = emin;
+  return true;
+}
+
+// Bit length of a nonzero unsigned 128-bit value.
+__device__ __forceinline__ int bitlen_u128(unsigned __int128 v) {
+  const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+  return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+}
+
+// Exact orientation in integer arithmetic only (GB300's FP64 rate is a small
+// fraction of its integer rate).  With the four coordinate differences exact
+// as q_i * 2^e_i (diff_as_int), det = q1 q4 2^(e1+e4) - q2 q3 2^(e2+e3) with
+// products of at most 126 bits: the signs decide unless both terms have the
+// same sign, then the magnitudes are compared by bit length and, when the
+// lengths agree, after aligning the exponents (a shift below the 128-bit
+// width).  Returns false (no result) when a difference is not representable
+// that way: the caller then takes the floating-point path.
+static __device__ __noinline__ bool orient_f64_int(double ax, double ay, double bx, double by, double cx,
+                                                   double cy, int& sign) {
+  long long q1, q2, q3, q4;
+  int e1, e2, e3, e4;
+  // det = (ax - cx)(by - cy) - (ay - cy)(bx - cx)
+  if (!diff_as_int(ax, cx, q1, e1) || !diff_as_int(by, cy, q4, e4) || !diff_as_int(ay, cy, q2, e2) ||
+      !diff_as_int(bx, cx, q3, e3))
+    return false;
+  const __int128 p1 = (__int128)q1 * q4, p2 = (__int128)q2 * q3;
+  const int s1 = (p1 > 0) - (p1 < 0), s2 = (p2 > 0) - (p2 < 0);
+  if (s1 == 0 || s2 == 0 || s1 != s2) { sign = s1 != 0 ? s1 : -s2; return true; }
+  const unsigned __int128 m1 = (unsigned __int128)(s1 > 0 ? p1 : -p1);
+  const unsigned __int128 m2 = (unsigned __int128)(s2 > 0 ? p2 : -p2);
+  const int E1 = e1 + e4, E2 = e2 + e3;
+  const int L1 = bitlen_u128(m1) + E1, L2 = bitlen_u128(m2) + E2;
+  int cmp;                                    // sign of |p1| 2^E1 - |p2| 2^E2
+  if (L1 != L2) {
+    cmp = L1 > L2 ? 1 : -1;
+  } else {
+    // equal lengths: the exponent gap is the bit-length gap (< 127)
+    const unsigned __int128 a1 = E1 >= E2 ? m1 << (E1 - E2) : m1;
+    const unsigned __int128 a2 = E2 > E1 ? m2 << (E2 - E1) : m2;
+    cmp = a1 > a2 ? 1 : a1 < a2 ? -1 : 0;
+  }
+  sign = s1 > 0 ? cmp : -cmp;
+  return true;
+}
+
+// Exact orientation: the integer path when the coordinate differences allow
+// it (close points: the usual case for the near-degenerate triples that reach
+// this point), else the FP64 filter with Shewchuk's bound
+// (3 + 16 eps) eps (|l| + |r|), eps = 2^-53, then the expansion.  Valid for
+// coordinates that are 0 or of magnitude in [2^-400, 2^400] (no underflow or
+// overflow anywhere).
 __device__ __forceinline__ int orient_f64(double ax, double ay, double bx, double by,
                                           double cx, double cy) {
+  int sgn;
+  if (orient_f64_int(ax, ay, bx, by, cx, cy, sgn)) return sgn;
   double l = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
   double r = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
   double d = __dsub_rn(l, r);
@@ -487,6 +578,11 @@ __device__ __forceinline__ int orient_f64_split(double2 a, double2 b, double2 c,
 __device__ __forceinline__ uint64_t ld_acq_u64(const uint64_t* p) {
   uint64_t v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_rlx_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_rel_u64(uint64_t* p, uint64_t v) {
@@ -717,14 +813,16 @@ __device__ __forceinline__ void move_subslots(const Job& j, const Ws& w, const S
         for (int q = 0; q < 4; q++) b[q] = pos[q] + __shfl_sync(0xFFFFFFFFu, pre[q], l);
         const uint32_t nl = __shfl_sync(0xFFFFFFFFu, n, l);
         const int64_t sl = sd.off + (gs + l) * sub;
+#pragma unroll 2
         for (uint32_t i0 = 0; i0 < nl; i0 += 32) {
           const uint32_t i = i0 + lane;
           const bool ok = i < nl;
+          // the three loads do not wait on one another
           const uint32_t val = ok ? w.valB[sl + i] : 0u;
+          const uint64_t key = ok ? w.keyB[sl + i] : 0ull;
+          const uint64_t spv = ok ? w.spvB[sl + i] : 0ull;
           const int r = ok ? (int)(val >> 30) : -1;
           const bool mv = rsel < 0 ? ok : r == rsel;
-          const uint64_t key = mv ? w.keyB[sl + i] : 0ull;
-          const uint64_t spv = mv ? w.spvB[sl + i] : 0ull;
 #pragma unroll
           for (int q = 0; q < 4; q++) {
             if (rsel >= 0 && q != rsel) continue;
@@ -799,6 +897,8 @@ void launch_extract_spa(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_
 int launch_spa_blocked(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st);
 int extremes_blocks_per_sm(int dtype);
 void count_launches(uint64_t n);   // add to the library's launch counter (cch_launch_count)
+Tune tune_for(int dtype, int64_t npts, int32_t nsets);   // run-time choices of a call (tune.cu)
+int tune_bucket(int64_t npts, int32_t nsets);
 void serve_release_pinned();   // free the server's pooled pinned host buffers
 
 }  // namespace cch

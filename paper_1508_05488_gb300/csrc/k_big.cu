@@ -343,19 +343,35 @@ __device__ void big_pass(const Job& j, const Ws& w, int p, uint32_t total) {
         st_rel_u64(st, lb_pack(tag, 2, run));
       } else {
         st_rel_u64(st, lb_pack(tag, 1, run));
+        // Decoupled look-back over the digit's words of the predecessor
+        // tiles, eight of them per step (their loads in flight together):
+        // aggregates add up until an inclusive prefix ends the walk.  A
+        // word packs tag, kind and value, so a relaxed load reads a
+        // consistent triple.
         int64_t t = (int64_t)tile - 1;
         uint32_t spins = 0;
         while (t >= (int64_t)first) {
-          uint64_t v = ld_acq_u64(w.st_sort + (size_t)t * 256 + d);
-          uint32_t hi = (uint32_t)(v >> 32);
-          uint32_t kind = (hi >> 16) == tag ? (hi & 0xFFFFu) : 0u;
-          if (kind == 0) {
-            if (!spin_step(spins, w.ctr)) break;
-            continue;
+          constexpr int kLb = 8;
+          uint64_t v[kLb];
+#pragma unroll
+          for (int u = 0; u < kLb; u++)
+            v[u] = t - u >= (int64_t)first ? ld_rlx_u64(w.st_sort + (size_t)(t - u) * 256 + d)
+                                           : lb_pack(tag, 2, 0);
+          int used = 0;
+          bool incl = false, stall = false;
+#pragma unroll
+          for (int u = 0; u < kLb; u++) {
+            if (incl || stall) continue;
+            const uint32_t hi = (uint32_t)(v[u] >> 32);
+            const uint32_t kind = (hi >> 16) == tag ? (hi & 0xFFFFu) : 0u;
+            if (kind == 0) { stall = true; continue; }
+            excl += (uint32_t)v[u];
+            used = u + 1;
+            incl = kind == 2;
           }
-          excl += (uint32_t)v;
-          if (kind == 2) break;
-          t--;
+          if (incl) break;
+          t -= used;
+          if (stall && !spin_step(spins, w.ctr)) break;
         }
         st_rel_u64(st, lb_pack(tag, 2, excl + run));
       }
@@ -444,7 +460,7 @@ __device__ void big_spa(const Job& j, const Ws& w) {
     if (lane == 31) wmin[warp] = x;
     __syncthreads();
     for (int q = 0; q < warp; q++) texcl = min(texcl, wmin[q]);
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
       uint64_t agg = ~0ull;
       for (int q = 0; q < kWarps; q++) agg = min(agg, wmin[q]);
       // start value: the region's first extreme
@@ -455,29 +471,50 @@ __device__ void big_spa(const Job& j, const Ws& w) {
       uint64_t excl = spa_value<DT>(e, r);
       SpaStat* st = w.st_spa + tile;
       if (lt == 0) {
-        st->inc_min = min(excl, agg);
-        st_rel_u32(&st->flag, (tag_min << 16) | 2u);
+        if (lane == 0) {
+          st->inc_min = min(excl, agg);
+          st_rel_u32(&st->flag, (tag_min << 16) | 2u);
+        }
       } else {
-        st->agg_min = agg;
-        st_rel_u32(&st->flag, (tag_min << 16) | 1u);
-        int64_t t = (int64_t)tile - 1;
+        if (lane == 0) {
+          st->agg_min = agg;
+          st_rel_u32(&st->flag, (tag_min << 16) | 1u);
+        }
+        // warp-cooperative decoupled look-back: lane l reads tile base - l;
+        // the minimum runs over the tiles up to the nearest inclusive prefix
+        int64_t base = (int64_t)tile - 1;
         uint32_t spins = 0;
-        while (t >= (int64_t)first) {
-          const SpaStat* q = w.st_spa + t;
-          uint32_t f = ld_acq_u32(&q->flag);
-          uint32_t kind = (f >> 16) == tag_min ? (f & 0xFFFFu) : 0u;
-          if (kind == 0) {
-            if (!spin_step(spins, w.ctr)) break;
+        while (base >= (int64_t)first) {
+          const int64_t t = base - lane;
+          uint32_t kind = 2u;
+          if (t >= (int64_t)first) {
+            const uint32_t f = ld_acq_u32(&w.st_spa[t].flag);
+            kind = (f >> 16) == tag_min ? (f & 0xFFFFu) : 0u;
+          }
+          const uint32_t incl = __ballot_sync(0xFFFFFFFFu, kind == 2u);
+          const int stop = incl ? __ffs(incl) - 1 : 31;
+          const uint32_t upto = stop == 31 ? 0xFFFFFFFFu : (2u << stop) - 1u;
+          if (__ballot_sync(0xFFFFFFFFu, kind == 0u) & upto) {
+            const bool go = spin_step(spins, w.ctr);   // identical in every lane
+            if (!__all_sync(0xFFFFFFFFu, go)) break;
             continue;
           }
-          if (kind == 2) { excl = min(excl, *(volatile const uint64_t*)&q->inc_min); break; }
-          excl = min(excl, *(volatile const uint64_t*)&q->agg_min);
-          t--;
+          uint64_t v = ~0ull;
+          if (lane <= stop && t >= (int64_t)first)
+            v = kind == 2u ? *(volatile const uint64_t*)&w.st_spa[t].inc_min
+                           : *(volatile const uint64_t*)&w.st_spa[t].agg_min;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+          excl = min(excl, v);
+          if (incl) break;
+          base -= 32;
         }
-        st->inc_min = min(excl, agg);
-        st_rel_u32(&st->flag, (tag_min << 16) | 2u);
+        if (lane == 0) {
+          st->inc_min = min(excl, agg);
+          st_rel_u32(&st->flag, (tag_min << 16) | 2u);
+        }
       }
-      sh_prefix = excl;
+      if (lane == 0) sh_prefix = excl;
     }
     __syncthreads();
     uint64_t run = min(sh_prefix, texcl);

@@ -279,10 +279,35 @@ __device__ __forceinline__ float sort_u(float X, float Y, int r) {
   }
 }
 
+// FP32 filter of the directed edge a -> b (see setup_set): coefficients of
+// orient(a, b, p) = A py - B px + C and the bound E on its FP32 evaluation
+// error; a degenerate edge (a = b) is always "inside", without the filter
+// (filt false) nothing is.
+__device__ void edge_filter(double ax, double ay, double bx, double by, double xm, double ym, bool filt,
+                            float& fA, float& fB, float& fC, float& fE) {
+  const double u = 5.9604644775390625e-08;
+  if (!filt) {
+    fA = 0.f; fB = 0.f; fC = 0.f; fE = __int_as_float(0x7F800000);
+  } else if (ax == bx && ay == by) {
+    fA = 0.f; fB = 0.f; fC = 1.f; fE = 0.f;
+  } else {
+    double A = bx - ax, B = by - ay;
+    double C = B * ax - A * ay;
+    double Mc = fabs(B) * fabs(ax) + fabs(A) * fabs(ay);
+    double E = 6.0 * u * (fabs(A) * ym + fabs(B) * xm + Mc)
+             + (fabs(A) + fabs(B)) * 2.350988701644575e-38      // 2^-125
+             + 3.5032461608120427e-45 * (xm + ym + 1.0);        // 2^-147
+    fA = __double2float_rn(A);
+    fB = __double2float_rn(B);
+    fC = __double2float_rn(C);
+    fE = __double2float_ru(E);
+  }
+}
+
 // Edge set-up of one set, run by one thread once E1..E4 are known.
 template <int DT>
 __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, const Lex best[4],
-                          uint32_t amin, uint32_t lomag) {
+                          uint32_t amin, uint32_t lomag, const uint64_t* dq) {
   SetCtl& c = w.ctl[s];
   using P = typename PointT<DT>::T;
   const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
@@ -314,47 +339,61 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
   for (int k = 0; k < 4; k++)
     if (c.eidx[k] == c.eidx[(k + 1) & 3]) flags |= SF_DEGEN0 << k;
   bool small = true;
+  // E1 = P_minx, E3 = P_maxx, E2 = P_miny, E4 = P_maxy
+  const double xm = fmax(fabs(c.ex[0]), fabs(c.ex[2]));
+  const double ym = fmax(fabs(c.ey[1]), fabs(c.ey[3]));
   if constexpr (DT == DT_I32) {
-    // E1 = P_minx, E3 = P_maxx, E2 = P_miny, E4 = P_maxy
     double spanx = c.ex[2] - c.ex[0], spany = c.ey[3] - c.ey[1];
     if (spanx >= 2147483648.0 || spany >= 2147483648.0) flags |= SF_WIDE;
   } else {
-    double xm = fmax(fabs(c.ex[0]), fabs(c.ex[2]));
-    double ym = fmax(fabs(c.ey[1]), fabs(c.ey[3]));
     const double lim = 1152921504606846976.0;  // 2^60
     small = xm <= lim && ym <= lim;
     if (small) flags |= SF_SMALL;
     // every coordinate of magnitude in [2^-126, 2^60]: the short FP32 view
     // (f32_view_short) equals f64_trunc_f32
     if (small && lomag >= kTinyTopBits) flags |= SF_SHORTVIEW;
+  }
+  {
     const bool filt = small && !(j.opts & OPT_NO_FILTER);
     if (filt) flags |= SF_FILTER;
     // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
-    // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on
-    // significand-truncated X, Y differs from the exact value by at most
-    // 5.01 u (|A| Ymax + |B| Xmax + |B||ax| + |A||ay|) plus underflow terms,
-    // u = 2^-24; E below uses 6 u and rounds up.  Without the filter every
-    // point takes the exact path (E = inf); a degenerate edge is always
-    // "inside" (A = B = 0, C = 1, E = 0).
-    const double u = 5.9604644775390625e-08;
+    // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on the
+    // FP32 views X, Y (float64: significand-truncated, |X - x| < 2^-23 |x|;
+    // int32: rounded to nearest, |X - x| <= 2^-24 |x|) differs from the exact
+    // value by at most 5.01 u (|A| Ymax + |B| Xmax + |B||ax| + |A||ay|) plus
+    // underflow terms, u = 2^-24; E below uses 6 u and rounds up.  Without
+    // the filter every point takes the exact path (E = inf); a degenerate
+    // edge is always "inside" (A = B = 0, C = 1, E = 0).
     for (int k = 0; k < 4; k++) {
-      int k1 = (k + 1) & 3;
-      if (!filt) {
-        c.fA[k] = 0.f; c.fB[k] = 0.f; c.fC[k] = 0.f; c.fE[k] = __int_as_float(0x7F800000);
-      } else if (flags & (SF_DEGEN0 << k)) {
-        c.fA[k] = 0.f; c.fB[k] = 0.f; c.fC[k] = 1.f; c.fE[k] = 0.f;
-      } else {
-        double ax = c.ex[k], ay = c.ey[k], bx = c.ex[k1], by = c.ey[k1];
-        double A = bx - ax, B = by - ay;
-        double C = B * ax - A * ay;
-        double Mc = fabs(B) * fabs(ax) + fabs(A) * fabs(ay);
-        double E = 6.0 * u * (fabs(A) * ym + fabs(B) * xm + Mc)
-                 + (fabs(A) + fabs(B)) * 2.350988701644575e-38      // 2^-125
-                 + 3.5032461608120427e-45 * (xm + ym + 1.0);        // 2^-147
-        c.fA[k] = __double2float_rn(A);
-        c.fB[k] = __double2float_rn(B);
-        c.fC[k] = __double2float_rn(C);
-        c.fE[k] = __double2float_ru(E);
+      const int k1 = (k + 1) & 3;
+      edge_filter(c.ex[k], c.ey[k], c.ex[k1], c.ey[k1], xm, ym, filt, c.fA[k], c.fB[k], c.fC[k], c.fE[k]);
+    }
+    if (dq) {
+      // Octagon (OPT_OCTAGON): vertex 2r is E_r, vertex 2r+1 the diagonal
+      // extreme D_r when it lies strictly outside edge r (exact test), else
+      // E_{r+1} (the edge D_r -> E_{r+1} is then degenerate).  Each kept D_r
+      // is the extreme of its direction among the set's FP32 scores, so the
+      // eight vertices in this order form a convex polygon inside the hull.
+      for (int r = 0; r < 4; r++) {
+        const int r1 = (r + 1) & 3;
+        c.ovx[2 * r] = c.ex[r];
+        c.ovy[2 * r] = c.ey[r];
+        c.didx[r] = -1;
+        double dx = c.ex[r1], dy = c.ey[r1];
+        if (!(flags & (SF_DEGEN0 << r)) && dq[r] != ~0ull) {
+          const uint32_t di = (uint32_t)dq[r];
+          const P d = pts[di];
+          int o;
+          if constexpr (DT == DT_F64) o = orient_f64(c.ex[r], c.ey[r], c.ex[r1], c.ey[r1], d.x, d.y);
+          else o = orient_i32((int)c.ex[r], (int)c.ey[r], (int)c.ex[r1], (int)c.ey[r1], d.x, d.y, true);
+          if (o < 0) { dx = (double)d.x; dy = (double)d.y; c.didx[r] = (int32_t)di; }
+        }
+        c.ovx[2 * r + 1] = dx;
+        c.ovy[2 * r + 1] = dy;
+      }
+      for (int k = 0; k < 8; k++) {
+        const int k1 = (k + 1) & 7;
+        edge_filter(c.ovx[k], c.ovy[k], c.ovx[k1], c.ovy[k1], xm, ym, filt, c.oA[k], c.oB[k], c.oC[k], c.oE[k]);
       }
     }
   }
@@ -389,7 +428,20 @@ __device__ __forceinline__ void consumers_sync() {
 // streams them through a ring of shared-memory stages with 1-D TMA bulk
 // copies (full/empty mbarriers); warps 0..7 each scan a contiguous eighth of
 // every tile, so every thread meets its points in increasing index order.
-template <int DT>
+// Diagonal extremes of the octagon mode (OPT_OCTAGON): per direction the
+// point with the smallest FP32 score of its views -- lower left X + Y, lower
+// right Y - X, upper right -X - Y, upper left X - Y -- ties to the smallest
+// index, as (order word of the score) << 32 | index.  Any input point is a
+// valid octagon vertex; the set-up keeps it only where it is strictly
+// outside the quadrilateral's edge.
+__device__ __forceinline__ void oct_update(uint64_t dq[4], float X, float Y, uint32_t i) {
+  dq[0] = min(dq[0], ((uint64_t)f32_order(__fadd_rn(X, Y)) << 32) | i);
+  dq[1] = min(dq[1], ((uint64_t)f32_order(__fsub_rn(Y, X)) << 32) | i);
+  dq[2] = min(dq[2], ((uint64_t)f32_order(-__fadd_rn(X, Y)) << 32) | i);
+  dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | i);
+}
+
+template <int DT, bool OCT>
 __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
@@ -403,6 +455,7 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   __shared__ int st_head[kExtStages];
   __shared__ Lex red[kClsConsumers][4];
   __shared__ uint32_t red_amin[kClsConsumers], red_lomag[kClsConsumers];
+  __shared__ uint64_t red_dq[kClsConsumers][4];
   __shared__ int last;
 
   const int chunk = blockIdx.x;
@@ -479,6 +532,7 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   a1_thresholds_f(best, thf);
   uint32_t amin = 0x7FFFFFFFu;      // smallest top-word magnitude of a nonzero coordinate
   uint32_t lomag = 0x7FFFFFFFu;     // the same over every coordinate, zeros included (float64)
+  uint64_t dqm[4] = {~0ull, ~0ull, ~0ull, ~0ull};   // OCT: diagonal extremes
   // set-local indices fit in 32 bits (n <= 2^30)
   for (int it = 0; it < ntile; it++) {
     const int slot = it % kExtStages;
@@ -505,6 +559,9 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
         if (i < np) {
           const uint4 q = *reinterpret_cast<const uint4*>(base + i * PB);
           xl[k] = q.x; xh[k] = q.y; yl[k] = q.z; yh[k] = q.w;
+          if constexpr (OCT)
+            oct_update(dqm, f64_trunc_f32(((uint64_t)q.y << 32) | q.x), f64_trunc_f32(((uint64_t)q.w << 32) | q.z),
+                       i0 + (uint32_t)i);
           const float fx = __uint_as_float(q.y), fy = __uint_as_float(q.w);
           const bool pass = !(fx > thf[0]) | !(fy > thf[1]) | !(fx < thf[2]) | !(fy < thf[3]);
           const bool tiny = (fabsf(fx) < kTinyTopF) | (fabsf(fy) < kTinyTopF);
@@ -554,6 +611,11 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
       if (i < np) {
         const P p = *reinterpret_cast<const P*>(base + i * PB);
         a1_words<DT>(p, xh[k], xl[k], yh[k], yl[k], amin);
+        if constexpr (OCT) {
+          float X, Y;
+          f32_view<DT>(p, X, Y);
+          oct_update(dqm, X, Y, i0 + (uint32_t)i);
+        }
         need |= a1_maybe(xh[k], yh[k], th);
       } else {
         xh[k] = yh[k] = 0xFFFFFFFFu;
@@ -581,12 +643,18 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
     amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
     lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
+    if constexpr (OCT) {
+#pragma unroll
+      for (int q = 0; q < 4; q++) dqm[q] = min(dqm[q], __shfl_xor_sync(0xFFFFFFFFu, dqm[q], o));
+    }
   }
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
     red_amin[warp] = amin;
     red_lomag[warp] = lomag;
+#pragma unroll
+    for (int q = 0; q < 4; q++) red_dq[warp][q] = dqm[q];
   }
   consumers_sync();
   if (tid == 0) {
@@ -594,11 +662,13 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
       amin = min(amin, red_amin[q]);
       lomag = min(lomag, red_lomag[q]);
+      for (int k = 0; k < 4; k++) dqm[k] = min(dqm[k], red_dq[q][k]);
     }
     Part& pt = w.part[chunk];
     for (int k = 0; k < 4; k++) { pt.k1[k] = best[k].k1; pt.k2[k] = best[k].k2; pt.idx[k] = best[k].idx; }
     pt.bad = amin;
     pt.lomag = lomag;
+    for (int k = 0; k < 4; k++) pt.dq[k] = dqm[k];
     __threadfence();
     last = atomicAdd(&w.ctl[s].arrive1, 1u) == (uint32_t)(sd.nchunk1 - 1);
   }
@@ -616,6 +686,7 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
   amin = 0x7FFFFFFFu;
   lomag = 0x7FFFFFFFu;
+  for (int k = 0; k < 4; k++) dqm[k] = ~0ull;
   for (int q = threadIdx.x; q < sd.nchunk1; q += kClsConsumers * 32) {
     const Part& pt = w.part[sd.chunk1 + q];
     for (int k = 0; k < 4; k++) {
@@ -624,6 +695,8 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     }
     amin = min(amin, pt.bad);
     lomag = min(lomag, pt.lomag);
+    if constexpr (OCT)
+      for (int k = 0; k < 4; k++) dqm[k] = min(dqm[k], pt.dq[k]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -631,6 +704,10 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
     amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
     lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
+    if constexpr (OCT) {
+#pragma unroll
+      for (int q = 0; q < 4; q++) dqm[q] = min(dqm[q], __shfl_xor_sync(0xFFFFFFFFu, dqm[q], o));
+    }
   }
   consumers_sync();
   if (lane == 0) {
@@ -638,6 +715,8 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
     red_amin[warp] = amin;
     red_lomag[warp] = lomag;
+#pragma unroll
+    for (int q = 0; q < 4; q++) red_dq[warp][q] = dqm[q];
   }
   consumers_sync();
   if (threadIdx.x == 0) {
@@ -645,8 +724,9 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
       for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
       amin = min(amin, red_amin[q]);
       lomag = min(lomag, red_lomag[q]);
+      for (int k = 0; k < 4; k++) dqm[k] = min(dqm[k], red_dq[q][k]);
     }
-    setup_set<DT>(j, w, s, sd, best, amin, lomag);
+    setup_set<DT>(j, w, s, sd, best, amin, lomag, OCT ? dqm : nullptr);
   }
 }
 
@@ -704,7 +784,7 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   for (int i = threadIdx.x; i < 4 * kTb; i += kThreads) (&tb[0][0])[i] = 0xFFFFFFFFu;
   __syncthreads();
 
-  const int64_t m = stairs_sample(sd.n);
+  const int64_t m = stairs_sample(sd.n, j.tune);
   const int64_t c0 = sd.n - m + (int64_t)(chunk - sd.chunk3) * kStairChunk;
   const int64_t c1 = min(sd.n, c0 + kStairChunk);
   const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
@@ -926,14 +1006,48 @@ struct WarpParams {
   int ix[4], iy[4];
 };
 
+// Octagon mode: certainly strictly inside all eight octagon edges by their
+// FP32 filters (oct[k] = A, -B, C, E of edge k, a shared-memory copy).
+__device__ __forceinline__ bool oct_inside_f32(const float4* oct, float X, float Y) {
+  bool in = true;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const float4 e = oct[k];
+    in &= __fmaf_rn(e.x, Y, __fmaf_rn(e.y, X, e.z)) > e.w;
+  }
+  return in;
+}
+
+// Octagon mode, exact: strictly inside all eight edges (degenerate edges
+// skipped), the FP32 filter deciding where it can.
+template <int DT>
+__device__ bool oct_inside_exact(const float4* oct, const SetCtl& c, float X, float Y,
+                                 const typename PointT<DT>::T& p) {
+#pragma unroll 1
+  for (int k = 0; k < 8; k++) {
+    const int k1 = (k + 1) & 7;
+    const double ax = c.ovx[k], ay = c.ovy[k], bx = c.ovx[k1], by = c.ovy[k1];
+    if (ax == bx && ay == by) continue;
+    const float4 e = oct[k];
+    const float d = __fmaf_rn(e.x, Y, __fmaf_rn(e.y, X, e.z));
+    if (d > e.w) continue;
+    if (d < -e.w) return false;
+    int o;
+    if constexpr (DT == DT_F64) o = orient_f64(ax, ay, bx, by, p.x, p.y);
+    else o = orient_i32((int)ax, (int)ay, (int)bx, (int)by, p.x, p.y, true);
+    if (o <= 0) return false;
+  }
+  return true;
+}
+
 // a2 pass 1 of a float64 tile slice (items k = 0 .. IW-1 of this lane, point
 // wb + 32 k + lane): bit k of the result is set unless the point is certainly
 // inside the quadrilateral (FP32 filter of the four edges) or strictly inside
 // the dominance box; the point's FP32 view goes to vbw[32 k + lane].  SHORT
 // selects the three-operation FP32 view.
-template <bool SHORT, int IW>
+template <bool SHORT, bool OCT, int IW>
 __device__ __forceinline__ uint32_t a2_pass1_f64(const unsigned char* base, int wb, int lane, int npv,
-                                                 const ClsParams& cp, uint2* vbw) {
+                                                 const ClsParams& cp, uint2* vbw, const float4* oct) {
   uint32_t nim = 0;
 #pragma unroll 4
   for (int k = 0; k < IW; k++) {
@@ -943,6 +1057,10 @@ __device__ __forceinline__ uint32_t a2_pass1_f64(const unsigned char* base, int 
       float X, Y;
       f32_view_a2<DT_F64, SHORT>(p, X, Y);
       vbw[k * 32 + lane] = make_uint2(__float_as_uint(X), __float_as_uint(Y));
+      if constexpr (OCT) {
+        nim |= (uint32_t)!oct_inside_f32(oct, X, Y) << k;
+        continue;
+      }
       const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
       const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
       const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
@@ -961,7 +1079,7 @@ __device__ __forceinline__ uint32_t a2_pass1_f64(const unsigned char* base, int 
 // tile, so (warp, item, lane) is point order, and compact their survivors
 // into their own sub-slot of the tile's record range (index order within the
 // sub-slot) -- no block-wide barrier on the per-tile path.
-template <int DT>
+template <int DT, bool OCT>
 __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
@@ -975,8 +1093,9 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kClsStages], empty[kClsStages];
   __shared__ int st_tile[kClsStages], st_set[kClsStages], st_head[kClsStages];
-  __shared__ uint16_t wq[kClsConsumers][IW * 32];     // pass-2 queue: int32 region << 9 | item << 5 | lane
+  __shared__ uint16_t wq[kClsConsumers][IW * 32];     // pass-2 queue: item << 5 | lane
   __shared__ uint2 vb[kClsConsumers][IW * 32];         // views (float64) / points (int32) of the warp's slice
+  __shared__ float4 woct[kClsConsumers][OCT ? 8 : 1];  // octagon mode: the edges' FP32 filters, per warp
   __shared__ WarpParams wpar[kClsConsumers];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1075,6 +1194,8 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
         wp.slo[lane] = c.slo[lane]; wp.ssc[lane] = c.sscale[lane];
         wp.ix[lane] = (int)c.ex[lane]; wp.iy[lane] = (int)c.ey[lane];
       }
+      if constexpr (OCT)
+        if (lane < 8) woct[warp][lane] = make_float4(c.oA[lane], -c.oB[lane], c.oC[lane], c.oE[lane]);
       __syncwarp();
       cp.bx0 = c.bx0; cp.bx1 = c.bx1; cp.by0 = c.by0; cp.by1 = c.by1;
       cp.flags = c.flags;
@@ -1097,33 +1218,31 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
     // the warp's view buffer, so that the stage can be released right after
     // this pass and the producer refills it while pass 2 runs.
     uint32_t nim = 0;                              // items that need pass 2
-    uint32_t ireg[IW > 8 ? 2 : 1] = {};            // int32: exact region, 4 bits per item
     uint2* vbw = vb[warp];
     if constexpr (DT == DT_F64) {
-      nim = shortv ? a2_pass1_f64<true, IW>(base, wb, lane, npv, cp, vbw)
-                   : a2_pass1_f64<false, IW>(base, wb, lane, npv, cp, vbw);
+      nim = shortv ? a2_pass1_f64<true, OCT, IW>(base, wb, lane, npv, cp, vbw, woct[warp])
+                   : a2_pass1_f64<false, OCT, IW>(base, wb, lane, npv, cp, vbw, woct[warp]);
     } else {
+      // the same FP32 filter on the rounded views; the buffer keeps the
+      // exact coordinates for pass 2
 #pragma unroll 4
       for (int k = 0; k < IW; k++) {
         const int i = wb + k * 32 + lane;
         if (i < npv) {
           const P p = *reinterpret_cast<const P*>(base + i * PB);
           vbw[k * 32 + lane] = make_uint2((uint32_t)p.x, (uint32_t)p.y);
-          uint32_t r = 0;
-          if (cp.flags & SF_WIDE) {
-            r = 15u;
-          } else {
-#pragma unroll
-            for (int q = 3; q >= 0; q--) {
-              if (!(cp.flags & (SF_DEGEN0 << q)) &&
-                  orient_i32(wp.ix[q], wp.iy[q], wp.ix[(q + 1) & 3], wp.iy[(q + 1) & 3], p.x, p.y, false) < 0)
-                r = (uint32_t)q + 1;
-            }
-          }
           const float X = __int2float_rn(p.x), Y = __int2float_rn(p.y);
-          if ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1)) r = 0;
-          ireg[k >> 3] |= r << (4 * (k & 7));
-          nim |= (uint32_t)(r != 0) << k;
+          if constexpr (OCT) {
+            nim |= (uint32_t)!oct_inside_f32(woct[warp], X, Y) << k;
+          } else {
+            const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
+            const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
+            const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
+            const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
+            const bool in = ((d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3])) |
+                            ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1));
+            nim |= (uint32_t)(!in) << k;
+          }
         }
       }
     }
@@ -1146,9 +1265,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
         const bool o = (nim >> k) & 1u;
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, o);
         if (o) {
-          uint32_t en = (uint32_t)(k << 5) | lane;
-          if constexpr (DT == DT_I32) en |= ((ireg[k >> 3] >> (4 * (k & 7))) & 0xFu) << 9;
-          q[nq + __popc(b & lt_mask)] = (uint16_t)en;
+          q[nq + __popc(b & lt_mask)] = (uint16_t)((k << 5) | lane);
         }
         nq += __popc(b);
       }
@@ -1185,12 +1302,27 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
               r = (uint32_t)region_exact_f64(p.x, p.y, cg.ex, cg.ey, cp.flags);
             }
           } else {
+            // exact region in 64-bit (128-bit for wide spans) integers
             p.x = (int)v.x;
             p.y = (int)v.y;
             X = __int2float_rn(p.x);
             Y = __int2float_rn(p.y);
-            r = (en >> 9) & 0xFu;
-            if (r == 15u) r = (uint32_t)region_exact_i32_wide(p.x, p.y, cg.ex, cg.ey, cp.flags);
+            if (cp.flags & SF_WIDE) {
+              r = (uint32_t)region_exact_i32_wide(p.x, p.y, cg.ex, cg.ey, cp.flags);
+            } else {
+#pragma unroll
+              for (int qq = 3; qq >= 0; qq--) {
+                if (!(cp.flags & (SF_DEGEN0 << qq)) &&
+                    orient_i32(wp.ix[qq], wp.iy[qq], wp.ix[(qq + 1) & 3], wp.iy[(qq + 1) & 3], p.x, p.y, false) < 0)
+                  r = (uint32_t)qq + 1;
+              }
+            }
+          }
+          if constexpr (OCT) {
+            if (r != 0) {
+              if constexpr (DT == DT_F64) p = gp[i];
+              if (oct_inside_exact<DT>(woct[warp], cg, X, Y, p)) r = 0;    // inside the octagon
+            }
           }
           if (r != 0 && (cp.flags & SF_STAIRS)) {
             const int qr = (int)r - 1;
@@ -1269,8 +1401,19 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
         t[q] = __reduce_add_sync(0xFFFFFFFFu, t[q]);
         p[q] = __reduce_add_sync(0xFFFFFFFFu, p[q]);
       }
-      if (lane == 0)
+      if (lane == 0) {
         for (int q = 0; q < 4; q++) { sh_tot[q] = t[q]; sh_cpre[q] = p[q]; }
+        if (lc == 0) {
+          // the set's first chunk records its region totals and its path
+          SetCtl& cs = w.ctl[s];
+          bool big = false;
+          for (int q = 0; q < 4; q++) { cs.cnt[q] = t[q]; big |= t[q] > (uint32_t)j.tune.small_max; }
+          cs.s1 = t[0] + t[1] + t[2] + t[3];
+          // the paper's chunked SPA reads the sorted records from global memory
+          if ((j.opts & OPT_BLOCKED_SPA) && cs.s1 > 0) big = true;
+          if (big) atomicOr(&cs.flags, (uint32_t)SF_BIG);
+        }
+      }
     }
     const int64_t nsub = (int64_t)sd.ntile2 * kClsConsumers;
     const int64_t g0 = (int64_t)lc * kPlanTiles * kClsConsumers + warp * kSubPerWarp;
@@ -1306,44 +1449,47 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
   __syncthreads();
   if (!sh_last) return;
   __threadfence();
-  for (int s2 = warp; s2 < j.nsets; s2 += kWarps) {
-    const SetDesc d2 = get_set(j, s2);
-    SetCtl& c2 = w.ctl[s2];
-    if (c2.status != 0) continue;                     // uniform across the warp
-    uint32_t t[4] = {0, 0, 0, 0};
-    for (int k = lane; k < d2.nchunkP; k += 32) {
-      const uint4 v = w.ptot[d2.chunkP + k];
-      t[0] += v.x; t[1] += v.y; t[2] += v.z; t[3] += v.w;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) t[q] = __reduce_add_sync(0xFFFFFFFFu, t[q]);
-    if (lane == 0) {
-      bool big = false;
-      for (int q = 0; q < 4; q++) { c2.cnt[q] = t[q]; big |= t[q] > (uint32_t)kSmallMax; }
-      c2.s1 = t[0] + t[1] + t[2] + t[3];
-      // the paper's chunked SPA reads the sorted records from global memory
-      if ((j.opts & OPT_BLOCKED_SPA) && c2.s1 > 0) big = true;
-      if (big) c2.flags |= SF_BIG;
-    }
-  }
-  __syncthreads();
+  // last CTA: the plans of both sort paths over all sets (block-wide scans;
+  // every set's region totals and path were recorded by its first chunk)
   plan_sort(j, w);
-  if (threadIdx.x == 0) {
-    uint32_t k = 0;
-    for (int s2 = 0; s2 < j.nsets; s2++) {
+  __shared__ uint32_t carry;
+  __shared__ uint32_t wsum[kWarps];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < j.nsets; base += kThreads) {
+    const int s2 = base + threadIdx.x;
+    uint32_t nseg = 0;
+    if (s2 < j.nsets) {
       const SetCtl& c2 = w.ctl[s2];
-      if (c2.status != 0 || (c2.flags & SF_BIG)) continue;
+      if (c2.status == 0 && !(c2.flags & SF_BIG))
+        for (int r = 0; r < 4; r++) nseg += c2.cnt[r] != 0;
+    }
+    uint32_t x = nseg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t k = carry + x - nseg;
+    for (int q = 0; q < warp; q++) k += wsum[q];
+    if (nseg) {
+      const SetCtl& c2 = w.ctl[s2];
       for (int r = 0; r < 4; r++)
         if (c2.cnt[r]) w.small_seg[k++] = (uint32_t)(4 * s2 + r);
     }
-    w.ctr[CT_SMALL_TOTAL] = k;
+    __syncthreads();
+    if (threadIdx.x == kThreads - 1) carry = k;
+    __syncthreads();
   }
+  if (threadIdx.x == 0) w.ctr[CT_SMALL_TOTAL] = carry;
 }
 
-template <int DT>
+template <int DT, bool OCT>
 static void extremes_attr() {
   static bool once = [] {
-    cudaFuncSetAttribute(k_extremes<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kExtSmem);
+    cudaFuncSetAttribute(k_extremes<DT, OCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kExtSmem);
     return true;
   }();
   (void)once;
@@ -1352,23 +1498,30 @@ static void extremes_attr() {
 int extremes_blocks_per_sm(int dtype) {
   int b = 0;
   if (dtype == DT_F64) {
-    extremes_attr<DT_F64>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_F64>, kExtBlock, kExtSmem);
+    extremes_attr<DT_F64, false>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_F64, false>, kExtBlock, kExtSmem);
   } else {
-    extremes_attr<DT_I32>();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_I32>, kExtBlock, kExtSmem);
+    extremes_attr<DT_I32, false>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_I32, false>, kExtBlock, kExtSmem);
   }
   return b > 0 ? b : 1;
 }
 
+template <int DT, bool OCT>
+static void launch_extremes_t(const Job& j, const Ws& w, const Launch& L) {
+  extremes_attr<DT, OCT>();
+  launch_pdl(k_extremes<DT, OCT>, j.nchunk1, kExtBlock, kExtSmem, L.stream, j, w);
+}
+
 int launch_extremes(const Job& j, const Ws& w, const Launch& L) {
   if (j.nchunk1 == 0) return 0;
+  const bool oct = (j.opts & OPT_OCTAGON) != 0;
   if (j.dtype == DT_F64) {
-    extremes_attr<DT_F64>();
-    launch_pdl(k_extremes<DT_F64>, j.nchunk1, kExtBlock, kExtSmem, L.stream, j, w);
+    if (oct) launch_extremes_t<DT_F64, true>(j, w, L);
+    else launch_extremes_t<DT_F64, false>(j, w, L);
   } else {
-    extremes_attr<DT_I32>();
-    launch_pdl(k_extremes<DT_I32>, j.nchunk1, kExtBlock, kExtSmem, L.stream, j, w);
+    if (oct) launch_extremes_t<DT_I32, true>(j, w, L);
+    else launch_extremes_t<DT_I32, false>(j, w, L);
   }
   return 1;
 }
@@ -1385,23 +1538,26 @@ int launch_gather(const Job& j, const Ws& w, const Launch& L) {
   return 1;
 }
 
+template <int DT, bool OCT>
+static void launch_classify_t(const Job& j, const Ws& w, const Launch& L, int grid) {
+  static bool once = [] {
+    cudaFuncSetAttribute(k_classify<DT, OCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT>());
+    return true;
+  }();
+  (void)once;
+  launch_pdl(k_classify<DT, OCT>, grid, kClsBlock, cls_smem_bytes<DT>(), L.stream, j, w);
+}
+
 int launch_classify(const Job& j, const Ws& w, const Launch& L) {
   int grid = j.ntile2 < L.cls_grid ? j.ntile2 : L.cls_grid;
   if (grid < 1) grid = 1;
+  const bool oct = (j.opts & OPT_OCTAGON) != 0;
   if (j.dtype == DT_F64) {
-    static bool once = [] {
-      cudaFuncSetAttribute(k_classify<DT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT_F64>());
-      return true;
-    }();
-    (void)once;
-    launch_pdl(k_classify<DT_F64>, grid, kClsBlock, cls_smem_bytes<DT_F64>(), L.stream, j, w);
+    if (oct) launch_classify_t<DT_F64, true>(j, w, L, grid);
+    else launch_classify_t<DT_F64, false>(j, w, L, grid);
   } else {
-    static bool once = [] {
-      cudaFuncSetAttribute(k_classify<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cls_smem_bytes<DT_I32>());
-      return true;
-    }();
-    (void)once;
-    launch_pdl(k_classify<DT_I32>, grid, kClsBlock, cls_smem_bytes<DT_I32>(), L.stream, j, w);
+    if (oct) launch_classify_t<DT_I32, true>(j, w, L, grid);
+    else launch_classify_t<DT_I32, false>(j, w, L, grid);
   }
   return 1;
 }

@@ -144,7 +144,8 @@ extern "C" int cch_hull_noalloc(const void* points, int64_t n, int dtype, int32_
   j.chunk1_len = len;
   j.nchunk1 = (int32_t)((n + len - 1) / len);
   j.ntile2 = (int32_t)((n + cls_tile(dtype) - 1) / cls_tile(dtype));
-  j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n) + kStairChunk - 1) / kStairChunk) : 0;
+  j.tune = kTuneDefault;
+  j.nchunk3 = n > 0 ? (int32_t)((stairs_sample(n, j.tune) + kStairChunk - 1) / kStairChunk) : 0;
   j.nchunkP = (j.ntile2 + kPlanTiles - 1) / kPlanTiles;
   j.sets = nullptr;
   j.one = SetDesc{0, n, 0, j.nchunk1, 0, j.ntile2, 0, j.nchunk3, 0, j.nchunkP};

@@ -182,6 +182,25 @@ def test_blocked_spa_of_the_paper(kind, n):
     assert np.array_equal(st["hull"], m["hull"])
 
 
+@pytest.mark.parametrize("kind,n", [(k, n) for k in STAGE_KINDS for n in (3_000, 60_001)])
+def test_octagon_round1(kind, n):
+    """Round 1 with the Akl-Toussaint octagon (cch_hull_stages opts bit 3):
+    the diagonal extremes, the round-1 sets and the SPA survivors equal the
+    oracle's restatement element by element (the paper's sets without the
+    points strictly inside the octagon), and the hull is unchanged."""
+    p = STAGE_KINDS[kind](n)
+    st = cch.stages(torch.from_numpy(p).to(DEV), octagon=True)
+    m = oracle.method(p)
+    diag = oracle.octagon_diag(p, m)
+    assert st["status"] == 0
+    assert st["diag"].tolist() == diag.tolist()
+    o = oracle.octagon_round1(p, diag, m)
+    for r in range(4):
+        assert np.array_equal(st["r1"][r], o["r1"][r]), ("round 1", r)
+        assert np.array_equal(st["spa"][r], o["spa"][r]), ("SPA", r)
+    assert np.array_equal(st["hull"], m["hull"])
+
+
 def test_prefilter_shrinks_round1_on_uniform_sets():
     for p in (inputs.square_f64(1_000_000, 5), inputs.disk_f64(1_000_000, 6)):
         t = torch.from_numpy(p).to(DEV)

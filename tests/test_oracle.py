@@ -326,6 +326,71 @@ def test_blocked_spa_closed_forms():
         assert np.array_equal(np.sort(keep[sub]), np.sort(oracle.hull(p)))
 
 
+# ------------------------------------------------ octagon round 1
+
+@pytest.mark.parametrize("seed", range(8))
+def test_diag_extremes_by_exact_scores(seed):
+    """On coordinates whose FP32 views and scores are exact (small integers,
+    coarse dyadic grids), the diagonal extremes are the exact minimisers of
+    x+y, y-x, -x-y, x-y with the smallest index on ties."""
+    rng = np.random.default_rng(700 + seed)
+    if seed % 2:
+        p = rng.integers(-50, 51, (400, 2)).astype(np.int32)
+    else:
+        p = (rng.integers(-400, 401, (400, 2)) / 16.0).astype(np.float64)
+    pl = [(Fraction(float(x)), Fraction(float(y))) for x, y in p.tolist()]
+    fs = [lambda q: q[0] + q[1], lambda q: q[1] - q[0], lambda q: -q[0] - q[1], lambda q: q[0] - q[1]]
+    want = [min(range(len(pl)), key=lambda i: (f(pl[i]), i)) for f in fs]
+    assert oracle.diag_extremes(p).tolist() == want
+
+
+def _strictly_inside_hull(verts_pts, q):
+    """q strictly inside the convex hull of verts_pts (exact rationals)."""
+    h = bf.hull(verts_pts)
+    if len(h) < 3:
+        return False
+    P = [verts_pts[i] for i in h]
+    return all(bf.orient(P[k], P[(k + 1) % len(P)], q) > 0 for k in range(len(P)))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_octagon_round1_against_brute_force(seed):
+    """A point is discarded by the octagon round 1 iff it is strictly inside
+    the convex hull of the eight vertices; every used D_r lies strictly
+    outside its quadrilateral edge; and the SPA survivors of the reduced
+    regions, computed by dominance, are the paper's survivors outside the
+    octagon (the octagon's interior never beats a point outside it)."""
+    rng = np.random.default_rng(800 + seed)
+    kind = seed % 3
+    if kind == 0:
+        p = inputs.disk_f64(300, 800 + seed)
+    elif kind == 1:
+        p = rng.integers(-12, 13, (300, 2)).astype(np.int32)
+    else:
+        p = (rng.integers(-40, 41, (300, 2)) / 8.0).astype(np.float64)
+    m = oracle.method(p)
+    diag = oracle.octagon_diag(p, m)
+    ext = [int(i) for i in m["ext"]]
+    pl = p.tolist()
+    for r in range(4):
+        if diag[r] >= 0:
+            assert bf.orient(pl[ext[r]], pl[ext[(r + 1) % 4]], pl[int(diag[r])]) < 0
+    o = oracle.octagon_round1(p, diag, m)
+    vpts = [pl[i] for i in o["verts"]]
+    region = bf.regions(p, ext)
+    red = list(region)
+    for i in range(len(pl)):
+        ins = _strictly_inside_hull(vpts, pl[i])
+        if region[i]:
+            assert (i not in set(o["r1"][region[i] - 1].tolist())) == ins, i
+        if ins:
+            red[i] = 0
+    spa = bf.spa_survivors(p, ext, red)
+    for k in range(4):
+        assert set(o["spa"][k].tolist()) == spa[k]
+        assert set(o["spa"][k].tolist()) == {i for i in m["spa"][k].tolist() if red[i]}
+
+
 # ------------------------------------------------ multi-core CPU baseline
 
 @pytest.mark.skipif(not oracle.parallel_available(), reason="gcc without OpenMP")
