@@ -56,7 +56,9 @@ constexpr int kStairB = 1024;          // buckets per region
 constexpr int64_t kStairSample = int64_t(1) << 20;   // sample points per set (the last ones)
 constexpr int kStairChunk = 4096;      // sample points per CTA
 constexpr int64_t kStairMin = 8192;    // smallest sample of a set
-constexpr int kPlanTiles = 64;         // a2 tiles per survivor-count chunk (one gather CTA)
+constexpr int kPlanTiles = 64;         // a2 tiles per survivor-count chunk
+constexpr int kGatherSplit = 8;        // gather CTAs per chunk (all of them move a dense chunk)
+constexpr int kGatherDense = 8192;     // survivors from which a chunk counts as dense
 // a1 reads the last kL2KeepBytes of every set without the evict-first hint,
 // so that they are still in L2 when k_stairs samples them (its sample is the
 // set's tail) and when a2 starts (a2 hands out its tiles from the last to the

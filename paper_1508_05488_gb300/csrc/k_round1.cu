@@ -1369,12 +1369,13 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
 
 __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
   griddep_enter();
-  constexpr int kSubPerWarp = kPlanTiles * kClsConsumers / kWarps;
-  __shared__ uint32_t sh_tot[4], sh_cpre[4];
-  __shared__ uint32_t wtot[kWarps][4];
+  constexpr int kChunkSub = kPlanTiles * kClsConsumers;     // sub-slots of a chunk
+  constexpr int kPartSub = kChunkSub / kGatherSplit;         // sub-slots of a part of a dense chunk
+  __shared__ uint32_t sh_tot[4], sh_cpre[4], sh_ct;
+  __shared__ uint32_t wtot[kWarps][4], wpre[kWarps][4];
   __shared__ int sh_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int chunk = blockIdx.x;
+  const int chunk = blockIdx.x / kGatherSplit, part = blockIdx.x % kGatherSplit;
   int s = 0;
   if (j.sets) {
     int lo = 0, hi = j.nsets - 1;
@@ -1403,7 +1404,9 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
       }
       if (lane == 0) {
         for (int q = 0; q < 4; q++) { sh_tot[q] = t[q]; sh_cpre[q] = p[q]; }
-        if (lc == 0) {
+        const uint4 cv = pt[lc];
+        sh_ct = cv.x + cv.y + cv.z + cv.w;
+        if (lc == 0 && part == 0) {
           // the set's first chunk records its region totals and its path
           SetCtl& cs = w.ctl[s];
           bool big = false;
@@ -1415,30 +1418,50 @@ __global__ void __launch_bounds__(kThreads) k_gather(Job j, Ws w) {
         }
       }
     }
-    const int64_t nsub = (int64_t)sd.ntile2 * kClsConsumers;
-    const int64_t g0 = (int64_t)lc * kPlanTiles * kClsConsumers + warp * kSubPerWarp;
-    const int64_t g1 = min(g0 + kSubPerWarp, nsub);
-    const uint64_t* tc = w.tcnt + (size_t)sd.tile2 * kClsConsumers;
-    uint32_t mt[4] = {0, 0, 0, 0};
-    for (int64_t g = g0 + lane; g < g1; g += 32) {
-      const uint64_t v = tc[g];
-#pragma unroll
-      for (int q = 0; q < 4; q++) mt[q] += (uint32_t)(v >> (16 * q)) & 0xFFFFu;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) mt[q] = __reduce_add_sync(0xFFFFFFFFu, mt[q]);
-    if (lane == 0)
-      for (int q = 0; q < 4; q++) wtot[warp][q] = mt[q];
     __syncthreads();
-    uint32_t pos[4], roff[4], acc = 0;
+    // A chunk with few survivors is moved by its first CTA alone; a dense
+    // one by all kGatherSplit CTAs of the chunk, each a part of its
+    // sub-slots (the survivors of the earlier parts are counted first).
+    const bool dense = sh_ct >= (uint32_t)kGatherDense;
+    if (dense || part == 0) {                          // uniform across the CTA
+      const int64_t nsub = (int64_t)sd.ntile2 * kClsConsumers;
+      const int64_t cs0 = (int64_t)lc * kChunkSub;
+      const int64_t a = dense ? cs0 + (int64_t)part * kPartSub : cs0;
+      const int per_warp = (dense ? kPartSub : kChunkSub) / kWarps;
+      const int64_t g0 = a + warp * per_warp;
+      const int64_t g1 = min(g0 + per_warp, nsub);
+      const uint64_t* tc = w.tcnt + (size_t)sd.tile2 * kClsConsumers;
+      uint32_t mt[4] = {0, 0, 0, 0}, mp[4] = {0, 0, 0, 0};
+      for (int64_t g = g0 + lane; g < g1; g += 32) {
+        const uint64_t v = tc[g];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      pos[q] = sh_cpre[q];
-      for (int v = 0; v < warp; v++) pos[q] += wtot[v][q];
-      roff[q] = acc;
-      acc += sh_tot[q];
+        for (int q = 0; q < 4; q++) mt[q] += (uint32_t)(v >> (16 * q)) & 0xFFFFu;
+      }
+      // the chunk's sub-slots before this CTA's part (none for part 0)
+      for (int64_t g = cs0 + threadIdx.x; g < min(a, nsub); g += kThreads) {
+        const uint64_t v = tc[g];
+#pragma unroll
+        for (int q = 0; q < 4; q++) mp[q] += (uint32_t)(v >> (16 * q)) & 0xFFFFu;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        mt[q] = __reduce_add_sync(0xFFFFFFFFu, mt[q]);
+        mp[q] = __reduce_add_sync(0xFFFFFFFFu, mp[q]);
+      }
+      if (lane == 0)
+        for (int q = 0; q < 4; q++) { wtot[warp][q] = mt[q]; wpre[warp][q] = mp[q]; }
+      __syncthreads();
+      uint32_t pos[4], roff[4], acc = 0;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        pos[q] = sh_cpre[q];
+        for (int v = 0; v < kWarps; v++) pos[q] += wpre[v][q];
+        for (int v = 0; v < warp; v++) pos[q] += wtot[v][q];
+        roff[q] = acc;
+        acc += sh_tot[q];
+      }
+      if (g0 < g1) move_subslots(j, w, sd, s, g0, g1, -1, pos, roff);
     }
-    if (g0 < g1) move_subslots(j, w, sd, s, g0, g1, -1, pos, roff);
   }
   // last CTA: region totals of every set, the path of every set, the plans
   __syncthreads();
@@ -1534,7 +1557,7 @@ int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
 }
 
 int launch_gather(const Job& j, const Ws& w, const Launch& L) {
-  launch_pdl(k_gather, j.nchunkP < 1 ? 1 : j.nchunkP, kThreads, 0, L.stream, j, w);
+  launch_pdl(k_gather, (j.nchunkP < 1 ? 1 : j.nchunkP) * kGatherSplit, kThreads, 0, L.stream, j, w);
   return 1;
 }
 
