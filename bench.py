@@ -434,34 +434,52 @@ def extra_configs_bench(cch, torch, dev, reps, hbm):
 SURVIVOR_SIZES = (100_000, 200_000, 500_000, 1_000_000, 2_000_000, 5_000_000, 10_000_000, 20_000_000)
 
 
-def f32soa_bench(cch, torch, host_square, reps):
-    """The paper's input form (Fig. 6: two float32 coordinate vectors): the
-    square set rounded to float32, through cch_hull_f32soa (exact widening
-    to float64, then the same pipeline), inputs resident on the device."""
+def f32soa_bench(cch, torch, host, reps):
+    """The paper's input form (Fig. 6: two float32 coordinate vectors): each
+    synthetic set rounded to float32, through cch_hull_f32soa (round 1 reads
+    the vectors, 8 bytes a point; later stages carry the exactly widened
+    float64 values), beside cch_hull on the same points as float64 pairs
+    (16 bytes a point).  Inputs resident on the device and larger than L2."""
     import numpy as np
-    p32 = host_square.astype(np.float32)
-    x = torch.from_numpy(np.ascontiguousarray(p32[:, 0])).cuda()
-    y = torch.from_numpy(np.ascontiguousarray(p32[:, 1])).cuda()
-    n = x.shape[0]
-    idx = torch.empty(n, dtype=torch.int32, device="cuda")
-    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
-    for _ in range(3):
-        cch.hull_f32soa_async(x, y, idx, cnt)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        cch.hull_f32soa_async(x, y, idx, cnt)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    h = int(cnt.item())
-    ref = cch.hull(torch.stack([x, y], 1).double())
-    same = h == ref.shape[0] and bool(torch.equal(idx[:h], ref))
-    del x, y, idx
-    return {"config": f"{n} float32 points of the square set as two coordinate vectors", "value": n / ms / 1e3,
-            "unit": "Mpoints/s", "ms_per_hull": ms, "hull_size": h, "identical_to_float64_path": same}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    sets = {}
+    for kind in [k for k in KINDS if k in host]:
+        p32 = host[kind].astype(np.float32)
+        x = torch.from_numpy(np.ascontiguousarray(p32[:, 0])).cuda()
+        y = torch.from_numpy(np.ascontiguousarray(p32[:, 1])).cuda()
+        n = x.shape[0]
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ms = timed(lambda: cch.hull_f32soa_async(x, y, idx, cnt))
+        h = int(cnt.item())
+        wide = torch.stack([x, y], 1).double()
+        idx64 = torch.empty(n, dtype=torch.int32, device="cuda")
+        cnt64 = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ms64 = timed(lambda: cch.hull_async(wide, idx64, cnt64))
+        same = h == int(cnt64.item()) and bool(torch.equal(idx[:h], idx64[:h]))
+        sets[kind] = {"mpoints_s": n / ms / 1e3, "ms_per_hull": ms, "float64_pairs_ms_per_hull": ms64,
+                      "hull_size": h, "identical_to_float64_path": same}
+        del x, y, idx, wide, idx64
+        torch.cuda.empty_cache()
+    if not sets:
+        return None
+    first = sets[next(iter(sets))]
+    n = next(iter(host.values())).shape[0]
+    return {"config": f"{n} float32 points of each synthetic set as two coordinate vectors",
+            "value": first["mpoints_s"], "value_set": next(iter(sets)), "unit": "Mpoints/s", "sets": sets}
 
 
 def survivors(kinds, sizes, reps):
@@ -544,7 +562,55 @@ def profile_run(args):
         print(json.dumps({"profile": "h2d", "bytes_per_copy_round": nbytes, "rounds": args.steps,
                           "gb_per_s_by_streams": out}))
         return 0
-    if args.profile == "batched":
+    if args.profile == "modes":
+        # the comparison modes on the 20M float64 sets: round 1 with the
+        # quadrilateral (the paper's), with the octagon, and with the dominance
+        # prefilters (this implementation's default); the paper's chunked SPA
+        # against the exact scan, both after the multi-block sort
+        rows = {}
+        for kind in KINDS:
+            d = torch.from_numpy(inputs.headline_f64(kind, args.n)).to(dev)
+            row = {}
+            for name, kw in (("prefiltered", {}), ("paper", {"prefilter": False}), ("octagon", {"octagon": True}),
+                             ("paper_blocked_spa", {"blocked": True})):
+                for _ in range(2):
+                    st = cch.stages(d, **kw)
+                cch.profile(True)
+                cch.profile_read()
+                for _ in range(args.steps):
+                    st = cch.stages(d, **kw)
+                ms, calls = cch.profile_read()
+                cch.profile(False)
+                ms = {k: v / max(calls, 1) for k, v in ms.items()}
+                row[name] = {"round1": int(st["counts"][0]), "spa": int(st["counts"][5:9].sum()),
+                             "hull": int(st["count"]), "radix_passes": st["passes"],
+                             "pipeline_ms": sum(v for k, v in ms.items() if k != "blocked_spa"),
+                             "stage_ms": {k: round(v, 4) for k, v in ms.items()}}
+            rows[kind] = row
+            del d
+            torch.cuda.empty_cache()
+        print(json.dumps({"profile": "modes", "n": args.n, "calls": args.steps, "sets": rows}))
+        return 0
+    if args.profile in ("hull", "hull_f32"):
+        # `--steps` hulls of each of `--kinds` at `--n` points: float64 pairs
+        # (`hull`) or the same points rounded to float32 vectors (`hull_f32`)
+        calls = []
+        for kind in args.kinds.split(","):
+            p = inputs.headline_f64(kind, args.n)
+            idx = torch.empty(args.n, dtype=torch.int32, device=dev)
+            cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+            if args.profile == "hull":
+                d = torch.from_numpy(p).to(dev)
+                calls.append(lambda d=d, idx=idx, cnt=cnt: cch.hull_async(d, idx, cnt))
+            else:
+                import numpy as np
+                p32 = p.astype(np.float32)
+                x = torch.from_numpy(np.ascontiguousarray(p32[:, 0])).to(dev)
+                y = torch.from_numpy(np.ascontiguousarray(p32[:, 1])).to(dev)
+                calls.append(lambda x=x, y=y, idx=idx, cnt=cnt: cch.hull_f32soa_async(x, y, idx, cnt))
+        cnt = None
+        call = lambda: [c() for c in calls]
+    elif args.profile == "batched":
         pts, off = inputs.batched_i32(args.batched_sets, seed=7)
         d = torch.from_numpy(pts).to(dev)
         n = int(off[-1])
@@ -568,7 +634,7 @@ def profile_run(args):
     e1.record()
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "calls": args.steps, "ms_per_call": e0.elapsed_time(e1) / args.steps,
-                      "count0": int(cnt[0])}))
+                      "count0": int(cnt[0]) if cnt is not None else None}))
     return 0
 
 
@@ -591,7 +657,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered load (0: skip the serving measurement)")
     ap.add_argument("--profile", default=None,
-                    help="profiling run: `batched` (the 4096-set call), `h2d` (pinned copy bandwidth) or a configuration name "
+                    help="profiling run: `hull` / `hull_f32` (`--kinds` at `--n`, float64 pairs or float32 "
+                         "vectors), `batched` (the 4096-set call), `h2d` (pinned copy bandwidth), `modes` "
+                         "(the round-1 and SPA comparison modes on the 20M sets) or a configuration name "
                          "(degenerate_20M, circle_2M, int32_1M): warm-up calls, then --steps calls, "
                          "one summary line, nothing else")
     ap.add_argument("--kinds", default=",".join(KINDS),
@@ -741,7 +809,7 @@ def main():
     cpu = None if args.no_cpu else cpu_baseline(host, args.cpu_n)
     del dpts, outs
     torch.cuda.empty_cache()
-    f32soa = f32soa_bench(cch, torch, host["square"], max(args.steps, 3)) if "square" in host else None
+    f32soa = f32soa_bench(cch, torch, host, max(args.steps, 3))
     torch.cuda.empty_cache()
     extra = None if args.no_extra else extra_configs_bench(cch, torch, dev, max(args.steps // 2, 5), hbm)
     torch.cuda.empty_cache()

@@ -111,17 +111,20 @@ int cch_hull_host(const void *points_host, int64_t n, int dtype,
 /*
  * The hull of points given as two float32 coordinate arrays, the input form
  * of the paper's implementation (Fig. 6 takes the coordinates as two float
- * vectors x and y).  Every float32 value widens exactly to float64 (sign,
- * rebiased exponent, significand shifted; subnormals normalised), so the
- * result is cch_hull's on the points (double(x[i]), double(y[i])): the same
- * indices, the same rules for duplicates, collinear points and -0.0.
- *   x, y       device float[n] each, 4-byte aligned; caller-owned
+ * vectors x and y).  Round 1 (the extremes, the quadrilateral test, region
+ * routing and the dominance prefilter) reads the two vectors directly,
+ * 8 bytes a point; its survivors and every later stage carry the points
+ * widened exactly to float64 (sign, rebiased exponent, significand shifted;
+ * subnormals normalised), so the result is cch_hull's on the points
+ * (double(x[i]), double(y[i])): the same indices, the same rules for
+ * duplicates, collinear points and -0.0.
+ *   x, y       device float[n] each, 4-byte aligned (any offset within a
+ *              16-byte line); caller-owned, read only
  *   n          0 <= n <= 2^30
  *   out_idx    device int32[max(n, 1)]; out_count device int32 (h, or a
  *              negative code: CCH_ERR_NONFINITE for NaN / Inf)
- * The widened copy (16 B per point) lives in a per-stream buffer the library
- * owns (grown on demand, freed by cch_release_workspace).  Asynchronous on
- * `stream`; host-detectable errors return before any launch.
+ * Uses the per-stream workspace of cch_hull.  Asynchronous on `stream`;
+ * host-detectable errors return before any launch.
  */
 int cch_hull_f32soa(const float *x, const float *y, int64_t n, int32_t *out_idx,
                     int32_t *out_count, void *stream);

@@ -187,8 +187,9 @@ def hull(points, stream=None):
 
 def hull_f32soa_async(x, y, out_idx=None, out_count=None, stream=None):
     """Enqueue the hull of the points (x[i], y[i]) given as two float32 CUDA
-    vectors (the paper's input form).  The coordinates widen exactly to
-    float64, so the result is hull_async's on torch.stack([x, y], 1).double().
+    vectors (the paper's input form).  Round 1 reads the two vectors
+    directly; later stages carry the coordinates widened exactly to float64,
+    so the result is hull_async's on torch.stack([x, y], 1).double().
     Returns (out_idx, out_count) device tensors as hull_async does."""
     import torch
     for t in (x, y):

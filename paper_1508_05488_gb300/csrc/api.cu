@@ -103,8 +103,6 @@ struct Workspace {
   int32_t* dcount = nullptr;         // device counts (cch_hull_host)
   int32_t* didx = nullptr;
   size_t didx_bytes = 0;
-  void* wide = nullptr;              // float64 copy of float32 SoA points (cch_hull_f32soa)
-  size_t wide_bytes = 0;
 };
 
 std::mutex g_mu;
@@ -126,7 +124,7 @@ cudaEvent_t* prof_begin(ProfRec& rec) {
   return rec.ev;
 }
 int g_sms = 0;
-int g_occ[3] = {0, 0, 0};
+int g_occ[4] = {0, 0, 0, 0};   // a1 CTAs per SM, by input format
 
 int sm_count() {
   if (g_sms == 0) {
@@ -174,9 +172,8 @@ int acquire(cudaStream_t stream, const Dims& d, Workspace** out) {
 }
 
 int a1_target(int dtype) {
-  int k = dtype == DT_F64 ? 1 : 2;
-  if (!g_occ[k]) g_occ[k] = extremes_blocks_per_sm(dtype);
-  return sm_count() * g_occ[k];
+  if (!g_occ[dtype]) g_occ[dtype] = extremes_blocks_per_sm(dtype);
+  return sm_count() * g_occ[dtype];
 }
 
 int grid_cap() { return sm_count() * 4; }
@@ -293,46 +290,6 @@ Job single_job(const void* points, int64_t n, int dtype, int32_t* out_idx, int32
 }
 
 // ------------------------------------------------ float32 SoA input
-
-// Exact float32 -> float64 widening from the IEEE 754 encodings: the sign
-// moves to bit 63, a normal exponent e becomes e - 127 + 1023, the 23-bit
-// significand moves to the top of the 52-bit one; a subnormal m * 2^-149 is
-// normalised (its leading 1 becomes the implicit bit); zero keeps its sign;
-// Inf / NaN keep exponent all-ones and the payload.  Integer operations only.
-__device__ __forceinline__ double widen_f32(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint64_t sign = (uint64_t)(u >> 31) << 63;
-  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  uint64_t bits;
-  if (e == 0xFFu) {
-    bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
-  } else if (e != 0) {
-    bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
-  } else if (m == 0) {
-    bits = sign;
-  } else {
-    const int p = 31 - __clz((int)m);                 // leading bit of m, 0..22
-    bits = sign | ((uint64_t)(p + 874) << 52) | (((uint64_t)m << (52 - p)) & ((1ull << 52) - 1));
-  }
-  return __longlong_as_double((long long)bits);
-}
-
-// Point i of the widened copy is written by one lane as one 16-byte store,
-// so a warp's loads (4 B per lane, per array) and stores (16 B per lane) are
-// contiguous.
-__global__ void __launch_bounds__(kThreads) k_widen(const float* __restrict__ x, const float* __restrict__ y,
-                                                    int64_t n, double2* __restrict__ out) {
-  const int64_t stride = (int64_t)gridDim.x * kThreads;
-  int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    float a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) { a[u] = x[i + u * stride]; b[u] = y[i + u * stride]; }
-#pragma unroll
-    for (int u = 0; u < 4; u++) out[i + u * stride] = make_double2(widen_f32(a[u]), widen_f32(b[u]));
-  }
-  for (; i < n; i += stride) out[i] = make_double2(widen_f32(x[i]), widen_f32(y[i]));
-}
 
 }  // namespace
 
@@ -467,32 +424,9 @@ int cch_hull_f32soa(const float* x, const float* y, int64_t n, int32_t* out_idx,
   if (n < 0 || !out_idx || !out_count || (n > 0 && (!x || !y))) return CCH_ERR_INVALID;
   if ((((uintptr_t)x | (uintptr_t)y) & 3u) != 0) return CCH_ERR_INVALID;
   if (n > kMaxSetPoints) return CCH_ERR_RANGE;
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t wbytes = 16 * (size_t)std::max<int64_t>(n, 1);
-  void* wide = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    Workspace*& ws = g_ws[s];
-    if (!ws) ws = new Workspace();
-    if (ws->wide_bytes < wbytes) {
-      if (ws->wide) { cudaStreamSynchronize(s); cudaFree(ws->wide); }
-      ws->wide = nullptr;
-      ws->wide_bytes = 0;
-      if (cudaMalloc(&ws->wide, wbytes) != cudaSuccess) { cudaGetLastError(); return CCH_ERR_NOMEM; }
-      ws->wide_bytes = wbytes;
-    }
-    wide = ws->wide;
-  }
-  if (n > 0) {
-    // the previous call on this stream is done with the buffer: a plain
-    // launch is ordered after all earlier work of the stream
-    const int64_t blocks = (n + 4 * kThreads - 1) / (4 * kThreads);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, 8 * (int64_t)sm_count()));
-    k_widen<<<grid, kThreads, 0, s>>>(x, y, n, reinterpret_cast<double2*>(wide));
-    g_launches += 1;
-    if (cudaGetLastError() != cudaSuccess) return CCH_ERR_CUDA;
-  }
-  return cch_hull(wide, n, CCH_F64, out_idx, out_count, stream);
+  Job j = single_job(x, n, DT_F32, out_idx, out_count, 0);
+  j.ys = y;
+  return run(j, nullptr, (cudaStream_t)stream, nullptr, nullptr);
 }
 
 int cch_hull_stages(const void* points, int64_t n, int dtype, uint32_t opts, int32_t* r1_idx,
@@ -615,7 +549,6 @@ void cch_release_workspace(void) {
     if (ws->h2d) cudaFree(ws->h2d);
     if (ws->dcount) cudaFree(ws->dcount);
     if (ws->didx) cudaFree(ws->didx);
-    if (ws->wide) cudaFree(ws->wide);
     delete ws;
   }
   g_ws.clear();

@@ -37,7 +37,11 @@ enum : int {
   ST_TIMEOUT = -7,
 };
 
-enum : int { DT_I32 = 1, DT_F64 = 2 };
+// Input formats.  DT_F32 (two float32 coordinate vectors) is read by the
+// round-1 kernels only: every later stage sees its points widened exactly to
+// float64 and runs the float64 code (the keys and SPA values it gets are the
+// float64 ones of the widened points).
+enum : int { DT_I32 = 1, DT_F64 = 2, DT_F32 = 3 };
 
 // ------------------------------------------------------------------ sizes
 constexpr int kThreads = 256;          // every kernel runs 256-thread CTAs
@@ -47,7 +51,9 @@ constexpr int kClsTileF64 = 2048;      // 32 KB
 constexpr int kClsTileI32 = 4096;      // 32 KB
 constexpr int kClsStages = 2;          // TMA ring depth of a2
 constexpr int kClsConsumers = 8;       // consumer warps of a2: each tile has 8 sub-slots
-__host__ __device__ constexpr int cls_tile(int dtype) { return dtype == 2 ? kClsTileF64 : kClsTileI32; }
+// a2 tile of an input format: 32 KB of points (float32 vectors and int32
+// pairs take 8 bytes a point, float64 pairs 16)
+__host__ __device__ constexpr int cls_tile(int dtype) { return dtype == DT_F64 ? kClsTileF64 : kClsTileI32; }
 constexpr int kClsMinTile = kClsTileF64 < kClsTileI32 ? kClsTileF64 : kClsTileI32;
 // SPA-dominance prefilter ("stairs"): per region, the prefix minimum of the
 // compared coordinate over buckets of the sort coordinate, built from a
@@ -144,7 +150,8 @@ struct SetDesc {
 // Per-call launch description.  A single hull carries its descriptor inline;
 // a batch points at a device array.
 struct Job {
-  const void* pts;      // [N,2] int32 or float64, device
+  const void* pts;      // [N,2] int32 or float64, device; DT_F32: the x vector, float[N]
+  const float* ys;      // DT_F32: the y vector, float[N]; nullptr otherwise
   int64_t N;            // total points
   int32_t nsets;
   int32_t dtype;
@@ -281,6 +288,51 @@ __device__ __forceinline__ uint64_t key_f64(uint64_t b) {
 }
 __device__ __forceinline__ uint64_t key_i32(int32_t v) {
   return (uint64_t)((uint32_t)v ^ 0x80000000u);
+}
+
+// Exact float32 -> float64 widening from the IEEE 754 encodings: the sign
+// moves to bit 63, a normal exponent e becomes e - 127 + 1023, the 23-bit
+// significand moves to the top of the 52-bit one; a subnormal m * 2^-149 is
+// normalised (its leading 1 becomes the implicit bit); zero keeps its sign;
+// Inf / NaN keep exponent all-ones and the payload.  Integer operations only.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  uint64_t bits;
+  if (e == 0xFFu) {
+    bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
+  } else if (e != 0) {
+    bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+  } else if (m == 0) {
+    bits = sign;
+  } else {
+    const int p = 31 - __clz((int)m);                 // leading bit of m, 0..22
+    bits = sign | ((uint64_t)(p + 874) << 52) | (((uint64_t)m << (52 - p)) & ((1ull << 52) - 1));
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// Order-preserving key of a float32 (-0.0 -> +0.0): the float64 key of its
+// widening has the same order.
+__device__ __forceinline__ uint32_t key_f32(float f) {
+  uint32_t u = __float_as_uint(f);
+  if ((u & 0x7FFFFFFFu) == 0) u = 0;
+  return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
+}
+
+// Point i of the input (set offset included) in the type the stages compute
+// in: float32 vectors widen to float64.
+template <typename P>
+__device__ __forceinline__ P input_point(const Job& j, int64_t i);
+template <>
+__device__ __forceinline__ double2 input_point<double2>(const Job& j, int64_t i) {
+  if (j.ys) return make_double2(widen_f32(reinterpret_cast<const float*>(j.pts)[i]), widen_f32(j.ys[i]));
+  return reinterpret_cast<const double2*>(j.pts)[i];
+}
+template <>
+__device__ __forceinline__ int2 input_point<int2>(const Job& j, int64_t i) {
+  return reinterpret_cast<const int2*>(j.pts)[i];
 }
 
 // a1 domain check of a float64 coordinate: 0, or 2^-400 <= |v| < 2^400.

@@ -206,7 +206,7 @@ __device__ __forceinline__ bool grid_sync(const Ws& w, uint32_t& gen) {
 __device__ void big_hist(const Job& j, const Ws& w, uint32_t total) {
   __shared__ uint32_t h[kSortPasses][256];
   const int lane = threadIdx.x & 31;
-  const int npass_key = j.dtype == DT_F64 ? 8 : 4;   // int32 keys have 4 zero bytes
+  const int npass_key = j.dtype != DT_I32 ? 8 : 4;   // int32 keys have 4 zero bytes
   for (uint32_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
     const int s = seg_of(w.sort_start, j.nsets, tile);
     const SetDesc sd = get_set(j, s);
@@ -403,7 +403,6 @@ __device__ void big_spa(const Job& j, const Ws& w) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = w.ctr[CT_SPA_TOTAL];
   const uint32_t tag_min = (j.epoch << 4) | 10u, tag_cnt = (j.epoch << 4) | 11u;
-  const P* pts_all = reinterpret_cast<const P*>(j.pts);
 
   for (;;) {
     if (threadIdx.x == 0) sh_tile = atomicAdd(w.ctr + CT_SPA_TILE, 1u);
@@ -427,7 +426,6 @@ __device__ void big_spa(const Job& j, const Ws& w) {
 
     // thread t owns records lt*2048 + t*8 .. +8 (contiguous: in-thread scan)
     const uint32_t b0 = lt * kSpaTile + threadIdx.x * kSpaItems;
-    const P* pts = pts_all + sd.off;
     uint32_t idx[kSpaItems];
     P pt[kSpaItems];
     uint64_t v[kSpaItems];
@@ -441,7 +439,7 @@ __device__ void big_spa(const Job& j, const Ws& w) {
     for (int k = 0; k < kSpaItems; k++) {
       uint32_t i = b0 + k;
       if (i < nr) {
-        pt[k] = pts[idx[k]];
+        pt[k] = input_point<P>(j, sd.off + idx[k]);
         v[k] = spa_value<DT>(pt[k], r);
       } else {
         v[k] = ~0ull;
@@ -632,12 +630,11 @@ __global__ void __launch_bounds__(kBlkThreads) k_spa_blocked(Job j, Ws w) {
   const uint32_t m = c.cnt[r];
   const uint32_t L = (m + kBlkThreads - 1) / kBlkThreads;
   const uint32_t b0 = threadIdx.x * L, b1 = min(m, b0 + L);
-  const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
   uint8_t* keep = reinterpret_cast<uint8_t*>(w.spvB) + sd.off + roff;
   uint64_t t = 0;
   uint32_t kept = 0;
   for (uint32_t i = b0; i < b1; i++) {
-    const uint64_t v = spa_value<DT>(pts[vin[sd.off + roff + i] & kIdxMask], r);
+    const uint64_t v = spa_value<DT>(input_point<P>(j, sd.off + (vin[sd.off + roff + i] & kIdxMask)), r);
     const bool k = i == b0 || v <= t;              // Fig. 2: discard only the strictly worse
     if (k) { t = v; kept++; }
     keep[i] = k ? 1 : 0;
@@ -686,7 +683,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_spa_blocked_out(Job j, Ws w, in
 }
 
 int launch_spa_blocked(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t st) {
-  if (j.dtype == DT_F64) {
+  if (j.dtype != DT_I32) {   // float32 input: the float64 stages
     launch_pdl(k_spa_blocked<DT_F64>, 4, kBlkThreads, 0, st, j, w);
     launch_pdl(k_spa_blocked_out<DT_F64>, 4, kBlkThreads, 0, st, j, w, spa_idx);
   } else {
@@ -698,8 +695,8 @@ int launch_spa_blocked(const Job& j, const Ws& w, int32_t* spa_idx, cudaStream_t
 
 int launch_big(const Job& j, const Ws& w, const Launch& L) {
   static int occ[3] = {0, 0, 0};
-  const int k = j.dtype == DT_F64 ? 1 : 2;
-  void* fn = j.dtype == DT_F64 ? (void*)k_big<DT_F64> : (void*)k_big<DT_I32>;
+  const int k = j.dtype != DT_I32 ? 1 : 2;   // float32 input: the float64 stages
+  void* fn = j.dtype != DT_I32 ? (void*)k_big<DT_F64> : (void*)k_big<DT_I32>;
   if (!occ[k]) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, 0) != cudaSuccess || b < 1) b = 1;

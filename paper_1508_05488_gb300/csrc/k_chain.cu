@@ -526,7 +526,7 @@ int launch_chain(const Job& j, const Ws& w, const Launch& L) {
   int grid = (int)(blks_max < L.grid_cap ? blks_max : L.grid_cap);
   if (grid < 1) grid = 1;
   int gridm = 4 * j.nsets < L.grid_cap ? 4 * j.nsets : L.grid_cap;
-  if (j.dtype == DT_F64) {
+  if (j.dtype != DT_I32) {   // float32 input: the float64 stages
     constexpr size_t sm = chain_local_smem<DT_F64>();
     static bool once = [] {
       cudaFuncSetAttribute(k_chain_local<DT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -46,6 +46,12 @@ template <>
 struct PointT<DT_F64> { using T = double2; };
 template <>
 struct PointT<DT_I32> { using T = int2; };
+template <>
+struct PointT<DT_F32> { using T = double2; };   // widened
+
+// Bytes a point takes in the input (float32: one word in each vector).
+template <int DT>
+constexpr int in_bytes() { return DT == DT_F64 ? 16 : 8; }
 
 // ------------------------------------------------------------- keys
 
@@ -208,15 +214,28 @@ __device__ __forceinline__ uint32_t f32_order(float f) {
 }
 
 // FP32 view of a point used by the filter and the stairs (truncated float64,
-// rounded int32): monotone in each coordinate.
+// rounded int32): monotone in each coordinate.  A float32 input is its own
+// view (view_at reads it from the vectors).
 template <int DT>
 __device__ __forceinline__ void f32_view(const typename PointT<DT>::T& p, float& X, float& Y) {
+  static_assert(DT != DT_F32, "float32 views come from view_at");
   if constexpr (DT == DT_F64) {
     X = f64_trunc_f32((uint64_t)__double_as_longlong(p.x));
     Y = f64_trunc_f32((uint64_t)__double_as_longlong(p.y));
   } else {
     X = __int2float_rn(p.x);
     Y = __int2float_rn(p.y);
+  }
+}
+
+// FP32 view of input point i (set offset included).
+template <int DT>
+__device__ __forceinline__ void view_at(const Job& j, int64_t i, float& X, float& Y) {
+  if constexpr (DT == DT_F32) {
+    X = reinterpret_cast<const float*>(j.pts)[i];
+    Y = j.ys[i];
+  } else {
+    f32_view<DT>(input_point<typename PointT<DT>::T>(j, i), X, Y);
   }
 }
 
@@ -237,26 +256,6 @@ __device__ __forceinline__ void f32_view_a2(const typename PointT<DT>::T& p, flo
     Y = f64_view_short((uint64_t)__double_as_longlong(p.y));
   } else {
     f32_view<DT>(p, X, Y);
-  }
-}
-
-// Compared-coordinate key (top word) of region r (0..3) in "smaller is
-// better" form: R1 y, R2 -x, R3 -y, R4 x.
-template <int DT>
-__device__ __forceinline__ uint32_t cmp_key_hi(const typename PointT<DT>::T& p, int r) {
-  uint32_t xh, yh;
-  if constexpr (DT == DT_F64) {
-    xh = f64_key_hi((uint64_t)__double_as_longlong(p.x));
-    yh = f64_key_hi((uint64_t)__double_as_longlong(p.y));
-  } else {
-    xh = (uint32_t)p.x ^ 0x80000000u;
-    yh = (uint32_t)p.y ^ 0x80000000u;
-  }
-  switch (r) {
-    case 0: return yh;
-    case 1: return ~xh;
-    case 2: return ~yh;
-    default: return xh;
   }
 }
 
@@ -310,18 +309,17 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
                           uint32_t amin, uint32_t lomag, const uint64_t* dq) {
   SetCtl& c = w.ctl[s];
   using P = typename PointT<DT>::T;
-  const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
   uint32_t flags = 0;
   P e[4];
   for (int k = 0; k < 4; k++) {
     c.ek1[k] = best[k].k1;
     c.ek2[k] = best[k].k2;
     c.eidx[k] = best[k].idx;
-    e[k] = pts[best[k].idx];
+    e[k] = input_point<P>(j, sd.off + best[k].idx);
     c.ex[k] = (double)e[k].x;
     c.ey[k] = (double)e[k].y;
   }
-  if constexpr (DT == DT_F64) {
+  if constexpr (DT != DT_I32) {
     // NaN, Inf and huge values sort beyond every finite value, so they show
     // up among the extremes; tiny nonzero values were folded into amin.
     int st = 0;
@@ -351,7 +349,7 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
     if (small) flags |= SF_SMALL;
     // every coordinate of magnitude in [2^-126, 2^60]: the short FP32 view
     // (f32_view_short) equals f64_trunc_f32
-    if (small && lomag >= kTinyTopBits) flags |= SF_SHORTVIEW;
+    if (DT == DT_F64 && small && lomag >= kTinyTopBits) flags |= SF_SHORTVIEW;
   }
   {
     const bool filt = small && !(j.opts & OPT_NO_FILTER);
@@ -359,7 +357,7 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
     // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
     // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on the
     // FP32 views X, Y (float64: significand-truncated, |X - x| < 2^-23 |x|;
-    // int32: rounded to nearest, |X - x| <= 2^-24 |x|) differs from the exact
+    // int32: rounded to nearest, |X - x| <= 2^-24 |x|; float32: exact) differs from the exact
     // value by at most 5.01 u (|A| Ymax + |B| Xmax + |B||ax| + |A||ay|) plus
     // underflow terms, u = 2^-24; E below uses 6 u and rounds up.  Without
     // the filter every point takes the exact path (E = inf); a degenerate
@@ -382,9 +380,9 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
         double dx = c.ex[r1], dy = c.ey[r1];
         if (!(flags & (SF_DEGEN0 << r)) && dq[r] != ~0ull) {
           const uint32_t di = (uint32_t)dq[r];
-          const P d = pts[di];
+          const P d = input_point<P>(j, sd.off + di);
           int o;
-          if constexpr (DT == DT_F64) o = orient_f64(c.ex[r], c.ey[r], c.ex[r1], c.ey[r1], d.x, d.y);
+          if constexpr (DT != DT_I32) o = orient_f64(c.ex[r], c.ey[r], c.ex[r1], c.ey[r1], d.x, d.y);
           else o = orient_i32((int)c.ex[r], (int)c.ey[r], (int)c.ex[r1], (int)c.ey[r1], d.x, d.y, true);
           if (o < 0) { dx = (double)d.x; dy = (double)d.y; c.didx[r] = (int32_t)di; }
         }
@@ -400,7 +398,7 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
   if (small && !(j.opts & OPT_NO_PREFILTER)) {
     flags |= SF_STAIRS;
     float X[4], Y[4];
-    for (int k = 0; k < 4; k++) f32_view<DT>(e[k], X[k], Y[k]);
+    for (int k = 0; k < 4; k++) view_at<DT>(j, sd.off + best[k].idx, X[k], Y[k]);
     // region r runs from E_r to E_{r+1} along its sort coordinate
     for (int r = 0; r < 4; r++) {
       int r1 = (r + 1) & 3;
@@ -415,8 +413,76 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
 
 constexpr int kExtStages = 3;                          // TMA ring depth of a1
 constexpr int kExtBlock = (kClsConsumers + 1) * 32;    // 8 consumer warps + a producer warp
-constexpr int kExtTileBytes = 32768;                    // a1 tiles: 2048 float64 / 4096 int32 points
-constexpr int kExtSmem = kExtStages * (kExtTileBytes + 16);
+constexpr int kExtTileBytes = 32768;                    // a1 tiles: 2048 float64 / 4096 int32 or float32 points
+constexpr int kExtSmem = kExtStages * (kExtTileBytes + 32);
+
+// Stage of a TMA ring: 16 bytes of slack, then the tile's points; float32
+// input: the x half, 16 bytes of slack, the y half (`half` bytes from the
+// stage start).
+//
+// Producer side of one tile: points [i0, i0 + np) of the input (set offset
+// included) into `stage`, the bytes counted on `bar`.  Bulk copies want
+// 16-byte aligned addresses and sizes, so the points before the first and
+// after the last 16-byte boundary of a vector (int32: at most one each;
+// float32: at most three each, per vector; float64: none, its input is
+// 16-byte aligned) go by plain loads into the slack and the tile's ends.
+// The number of leading points so moved (float32: x | y << 8) goes to
+// *lead before the arrive that can complete the stage (a tile without bulk
+// bytes completes on it): the consumers index the tile from 16 - that many
+// points into the stage.  `keep` drops the evict-first hint.
+__device__ __forceinline__ int f32_vec_part(const float* src, int np, unsigned char* dst, uint32_t& bytes,
+                                            const float*& body) {
+  const int mis = (int)(((uintptr_t)src >> 2) & 3u);
+  const int head = min(mis ? 4 - mis : 0, np);
+  const int rem = np - head;
+  const int tail = rem & 3;
+  float* d = reinterpret_cast<float*>(dst);
+  for (int t = 0; t < head; t++) d[t - head] = src[t];
+  for (int t = rem - tail; t < rem; t++) d[t] = src[head + t];
+  bytes = (uint32_t)(rem - tail) * 4u;
+  body = src + head;
+  return head;
+}
+
+template <int DT>
+__device__ __forceinline__ void stage_tile(const Job& j, int64_t i0, int np, unsigned char* stage, int half,
+                                           uint64_t* bar, bool keep, int* lead) {
+  if constexpr (DT == DT_F32) {
+    const float *bx, *by;
+    uint32_t nx, ny;
+    const int hx = f32_vec_part(reinterpret_cast<const float*>(j.pts) + i0, np, stage + 16, nx, bx);
+    const int hy = f32_vec_part(j.ys + i0, np, stage + half + 16, ny, by);
+    *lead = hx | (hy << 8);
+    mbar_arrive_tx(bar, nx + ny);
+    if (nx) {
+      if (keep) tma_load_1d(stage + 16, bx, nx, bar);
+      else tma_load_1d_stream(stage + 16, bx, nx, bar);
+    }
+    if (ny) {
+      if (keep) tma_load_1d(stage + half + 16, by, ny, bar);
+      else tma_load_1d_stream(stage + half + 16, by, ny, bar);
+    }
+  } else {
+    constexpr int PB = in_bytes<DT>();
+    const char* src = reinterpret_cast<const char*>(j.pts) + i0 * PB;
+    unsigned char* dst = stage + 16;
+    int head = 0, tail = 0;
+    if constexpr (DT == DT_I32) {
+      head = ((uintptr_t)src & 15) ? 1 : 0;
+      tail = (((np - head) * PB) & 15) ? 1 : 0;
+      if (head) *reinterpret_cast<uint2*>(dst - PB) = *reinterpret_cast<const uint2*>(src);
+      if (tail)
+        *reinterpret_cast<uint2*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const uint2*>(src + (size_t)(np - 1) * PB);
+    }
+    const uint32_t bytes = (uint32_t)(np - head - tail) * PB;
+    *lead = head;
+    mbar_arrive_tx(bar, bytes);
+    if (bytes) {
+      if (keep) tma_load_1d(dst, src + head * PB, bytes, bar);
+      else tma_load_1d_stream(dst, src + head * PB, bytes, bar);
+    }
+  }
+}
 
 // Barrier of the consumer warps only (the producer warp has left).
 __device__ __forceinline__ void consumers_sync() {
@@ -445,11 +511,13 @@ template <int DT, bool OCT>
 __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
-  constexpr int PB = (int)sizeof(P);
+  constexpr int PB = in_bytes<DT>();
   constexpr int TILE = kExtTileBytes / PB;
   constexpr int WPTS = TILE / kClsConsumers;
   constexpr int IW = WPTS / 32;
-  constexpr int SB = kExtTileBytes + 16;
+  constexpr int SB = kExtTileBytes + (DT == DT_F32 ? 32 : 16);
+  constexpr int HALF = kExtTileBytes / 2 + 16;
+  static_assert(SB * kExtStages <= kExtSmem, "a1 ring fits its allocation");
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kExtStages], empty[kExtStages];
   __shared__ int st_head[kExtStages];
@@ -496,20 +564,8 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
       }
       const int64_t i0 = (k0 + (int64_t)it * kstep) * TILE;
       const int np = (int)min((int64_t)TILE, sd.n - i0);
-      const char* src = reinterpret_cast<const char*>(j.pts) + (sd.off + i0) * PB;
-      unsigned char* dst = smem + slot * SB + 16;
-      const int head = ((uintptr_t)src & 15) ? 1 : 0;       // int32 only
-      const int rem = np - head;
-      const int tail = ((rem * PB) & 15) ? 1 : 0;
-      const uint32_t bytes = (uint32_t)(rem - tail) * PB;
-      st_head[slot] = head;
-      if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
-      if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
-      mbar_arrive_tx(&full[slot], bytes);
-      if (bytes) {
-        if ((sd.n - i0) * PB <= kL2KeepBytes) tma_load_1d(dst, src + head * PB, bytes, &full[slot]);
-        else tma_load_1d_stream(dst, src + head * PB, bytes, &full[slot]);
-      }
+      stage_tile<DT>(j, sd.off + i0, np, smem + slot * SB, HALF, &full[slot], (sd.n - i0) * PB <= kL2KeepBytes,
+                     &st_head[slot]);
       issued = it + 1;
     }
     if (!ok) {
@@ -548,7 +604,38 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     const int np = (int)min((int64_t)TILE, sd.n - t0);
     const unsigned char* base = smem + slot * SB + 16 - st_head[slot] * PB;
     const int wb = warp * WPTS;
-    if constexpr (DT == DT_F64) {
+    if constexpr (DT == DT_F32) {
+      // exact 32-bit keys of the two vectors, as for int32
+      const float* vx = reinterpret_cast<const float*>(smem + slot * SB + 16) - (st_head[slot] & 0xFF);
+      const float* vy = reinterpret_cast<const float*>(smem + slot * SB + HALF + 16) - (st_head[slot] >> 8);
+      uint32_t xh[IW], yh[IW];
+      bool need = false;
+#pragma unroll
+      for (int k = 0; k < IW; k++) {
+        const int i = wb + k * 32 + lane;
+        if (i < np) {
+          const float X = vx[i], Y = vy[i];
+          xh[k] = key_f32(X);
+          yh[k] = key_f32(Y);
+          if constexpr (OCT) oct_update(dqm, X, Y, i0 + (uint32_t)i);
+          need |= a1_maybe(xh[k], yh[k], th);
+        } else {
+          xh[k] = yh[k] = 0xFFFFFFFFu;
+        }
+      }
+      __syncwarp();
+      if (lane == 0)   // the warp is done with the stage: release it to the producer
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
+      if (__any_sync(0xFFFFFFFFu, need)) {
+#pragma unroll
+        for (int k = 0; k < IW; k++) {
+          const int i = wb + k * 32 + lane;
+          if (i < np && a1_maybe(xh[k], yh[k], th)) a1_update<DT>(xh[k], 0u, yh[k], 0u, i0 + i, best);
+        }
+        a1_thresholds(best, th);
+      }
+      continue;
+    } else if constexpr (DT == DT_F64) {
       // raw words; the filter and the small-magnitude test in FP32 on the
       // top words, the exact key work only where they fire
       uint32_t xh[IW], xl[IW], yh[IW], yl[IW];
@@ -602,37 +689,38 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
         a1_thresholds_f(best, thf);
       }
       continue;
-    }
-    uint32_t xh[IW], xl[IW], yh[IW], yl[IW];
-    bool need = false;
-#pragma unroll
-    for (int k = 0; k < IW; k++) {
-      const int i = wb + k * 32 + lane;
-      if (i < np) {
-        const P p = *reinterpret_cast<const P*>(base + i * PB);
-        a1_words<DT>(p, xh[k], xl[k], yh[k], yl[k], amin);
-        if constexpr (OCT) {
-          float X, Y;
-          f32_view<DT>(p, X, Y);
-          oct_update(dqm, X, Y, i0 + (uint32_t)i);
-        }
-        need |= a1_maybe(xh[k], yh[k], th);
-      } else {
-        xh[k] = yh[k] = 0xFFFFFFFFu;
-        xl[k] = yl[k] = 0u;
-      }
-    }
-    __syncwarp();
-    if (lane == 0)   // the warp is done with the stage: release it to the producer
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
-    // rare: a warp-uniform branch keeps the full update out of the hot path
-    if (__any_sync(0xFFFFFFFFu, need)) {
+    } else {
+      uint32_t xh[IW], xl[IW], yh[IW], yl[IW];
+      bool need = false;
 #pragma unroll
       for (int k = 0; k < IW; k++) {
         const int i = wb + k * 32 + lane;
-        if (i < np && a1_maybe(xh[k], yh[k], th)) a1_update<DT>(xh[k], xl[k], yh[k], yl[k], i0 + i, best);
+        if (i < np) {
+          const P p = *reinterpret_cast<const P*>(base + i * PB);
+          a1_words<DT>(p, xh[k], xl[k], yh[k], yl[k], amin);
+          if constexpr (OCT) {
+            float X, Y;
+            f32_view<DT>(p, X, Y);
+            oct_update(dqm, X, Y, i0 + (uint32_t)i);
+          }
+          need |= a1_maybe(xh[k], yh[k], th);
+        } else {
+          xh[k] = yh[k] = 0xFFFFFFFFu;
+          xl[k] = yl[k] = 0u;
+        }
       }
-      a1_thresholds(best, th);
+      __syncwarp();
+      if (lane == 0)   // the warp is done with the stage: release it to the producer
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
+      // rare: a warp-uniform branch keeps the full update out of the hot path
+      if (__any_sync(0xFFFFFFFFu, need)) {
+#pragma unroll
+        for (int k = 0; k < IW; k++) {
+          const int i = wb + k * 32 + lane;
+          if (i < np && a1_maybe(xh[k], yh[k], th)) a1_update<DT>(xh[k], xl[k], yh[k], yl[k], i0 + i, best);
+        }
+        a1_thresholds(best, th);
+      }
     }
   }
 
@@ -759,7 +847,6 @@ __device__ __forceinline__ uint32_t region_excl_min(uint32_t v, uint32_t* sw) {
 template <int DT>
 __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   griddep_enter();
-  using P = typename PointT<DT>::T;
   constexpr int kTb = kStairB + kStairB / 32;   // padded table (one spare word in 32)
   static_assert(kThreads == 4 * 64 && kStairB == 64 * 16, "64 threads x 16 buckets per region");
   __shared__ uint32_t tb[4][kTb];
@@ -787,22 +874,20 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   const int64_t m = stairs_sample(sd.n, j.tune);
   const int64_t c0 = sd.n - m + (int64_t)(chunk - sd.chunk3) * kStairChunk;
   const int64_t c1 = min(sd.n, c0 + kStairChunk);
-  const P* pts = reinterpret_cast<const P*>(j.pts) + sd.off;
   uint64_t dq[4] = {~0ull, ~0ull, ~0ull, ~0ull};   // best score key << 32 | index per quadrant
   constexpr int U = 8;
   for (int64_t b0 = c0; b0 < c1; b0 += (int64_t)kThreads * U) {
-    P v[U];
+    float vx[U], vy[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       int64_t i = b0 + u * kThreads + threadIdx.x;
-      if (i < c1) v[u] = pts[i];
+      if (i < c1) view_at<DT>(j, sd.off + i, vx[u], vy[u]);
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
       int64_t i = b0 + u * kThreads + threadIdx.x;
       if (i >= c1) continue;
-      float X, Y;
-      f32_view<DT>(v[u], X, Y);
+      const float X = vx[u], Y = vy[u];
       // quadrant scores: lower-left x+y, lower-right y-x, upper-right -x-y,
       // upper-left x-y (smaller is further into the quadrant)
       dq[0] = min(dq[0], ((uint64_t)f32_order(__fadd_rn(X, Y)) << 32) | (uint32_t)i);
@@ -866,7 +951,7 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
     if (d0 && d1 && d2 && d3) {
       float X[4], Y[4];
       const uint64_t d[4] = {d0, d1, d2, d3};
-      for (int q = 0; q < 4; q++) f32_view<DT>(pts[(uint32_t)~d[q]], X[q], Y[q]);
+      for (int q = 0; q < 4; q++) view_at<DT>(j, sd.off + (uint32_t)~d[q], X[q], Y[q]);
       SetCtl& cw = w.ctl[s];
       cw.bx0 = fmaxf(X[0], X[3]);
       cw.bx1 = fminf(X[1], X[2]);
@@ -882,11 +967,8 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
     uint32_t mn = 0xFFFFFFFFu;
 #pragma unroll
     for (int q = 0; q < 16; q++) mn = min(mn, loc[q]);
-    P e;
-    if constexpr (DT == DT_F64) { e.x = c.ex[rr]; e.y = c.ey[rr]; }
-    else { e.x = (int)c.ex[rr]; e.y = (int)c.ey[rr]; }
     float EX, EY;
-    f32_view<DT>(e, EX, EY);
+    view_at<DT>(j, sd.off + c.eidx[rr], EX, EY);
     uint32_t ex = min(region_excl_min(mn, sw), cmp_view_order(EX, EY, rr));
     uint4 o[4];
 #pragma unroll
@@ -969,7 +1051,7 @@ __device__ __forceinline__ float sel4(const float (&a)[4], int r) {
 template <int DT>
 __device__ __forceinline__ uint64_t sort_key(const typename PointT<DT>::T& p, int r) {
   uint64_t kx, ky, m;
-  if constexpr (DT == DT_F64) {
+  if constexpr (DT != DT_I32) {
     kx = key_f64((uint64_t)__double_as_longlong(p.x));
     ky = key_f64((uint64_t)__double_as_longlong(p.y));
     m = ~0ull;
@@ -988,9 +1070,14 @@ __device__ __forceinline__ uint64_t sort_key(const typename PointT<DT>::T& p, in
 
 constexpr int kClsBlock = (kClsConsumers + 1) * 32;  // + one producer warp
 
+// a2 stage bytes (the layout of stage_tile)
+template <int DT>
+constexpr int cls_stage_bytes() {
+  return cls_tile(DT) * in_bytes<DT>() + (DT == DT_F32 ? 32 : 16);
+}
 template <int DT>
 constexpr int cls_smem_bytes() {
-  return kClsStages * (cls_tile(DT) * (DT == DT_F64 ? 16 : 8) + 16);
+  return kClsStages * cls_stage_bytes<DT>();
 }
 
 // Set parameters a consumer warp keeps in registers (the per-point filter);
@@ -1033,7 +1120,7 @@ __device__ bool oct_inside_exact(const float4* oct, const SetCtl& c, float X, fl
     if (d > e.w) continue;
     if (d < -e.w) return false;
     int o;
-    if constexpr (DT == DT_F64) o = orient_f64(ax, ay, bx, by, p.x, p.y);
+    if constexpr (DT != DT_I32) o = orient_f64(ax, ay, bx, by, p.x, p.y);
     else o = orient_i32((int)ax, (int)ay, (int)bx, (int)by, p.x, p.y, true);
     if (o <= 0) return false;
   }
@@ -1073,6 +1160,35 @@ __device__ __forceinline__ uint32_t a2_pass1_f64(const unsigned char* base, int 
   return nim;
 }
 
+// The same pass on a float32 tile slice (vx, vy: the stage's two halves).
+// The values are their own FP32 views, and the view buffer keeps them: pass 2
+// widens them again where it needs exact coordinates.
+template <bool OCT, int IW>
+__device__ __forceinline__ uint32_t a2_pass1_f32(const float* vx, const float* vy, int wb, int lane, int npv,
+                                                 const ClsParams& cp, uint2* vbw, const float4* oct) {
+  uint32_t nim = 0;
+#pragma unroll 4
+  for (int k = 0; k < IW; k++) {
+    const int i = wb + k * 32 + lane;
+    if (i < npv) {
+      const float X = vx[i], Y = vy[i];
+      vbw[k * 32 + lane] = make_uint2(__float_as_uint(X), __float_as_uint(Y));
+      if constexpr (OCT) {
+        nim |= (uint32_t)!oct_inside_f32(oct, X, Y) << k;
+        continue;
+      }
+      const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
+      const float d1 = __fmaf_rn(cp.fA[1], Y, __fmaf_rn(cp.fB[1], X, cp.fC[1]));
+      const float d2 = __fmaf_rn(cp.fA[2], Y, __fmaf_rn(cp.fB[2], X, cp.fC[2]));
+      const float d3 = __fmaf_rn(cp.fA[3], Y, __fmaf_rn(cp.fB[3], X, cp.fC[3]));
+      const bool in = ((d0 > cp.fE[0]) & (d1 > cp.fE[1]) & (d2 > cp.fE[2]) & (d3 > cp.fE[3])) |
+                      ((X > cp.bx0) & (X < cp.bx1) & (Y > cp.by0) & (Y < cp.by1));
+      nim |= (uint32_t)(!in) << k;
+    }
+  }
+  return nim;
+}
+
 // a2.  Warp-specialised: warp 8 acquires tiles (in increasing order) and
 // streams them into a ring of shared-memory stages with 1-D TMA bulk copies
 // (full/empty mbarriers); warps 0..7 each classify a contiguous eighth of the
@@ -1083,18 +1199,19 @@ template <int DT, bool OCT>
 __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
   griddep_enter();
   using P = typename PointT<DT>::T;
-  constexpr int PB = (int)sizeof(P);
+  constexpr int PB = in_bytes<DT>();
   constexpr int TILE = cls_tile(DT);
   static_assert(TILE % (32 * kClsConsumers) == 0, "a tile is a whole number of items per consumer lane");
   constexpr int WPTS = TILE / kClsConsumers;          // points per consumer warp
   constexpr int IW = WPTS / 32;                       // items per lane
   static_assert(IW <= 16, "pass-2 queue entries hold the item in 4 bits");
-  constexpr int SB = TILE * PB + 16;                  // stage bytes (16 bytes of slack in front)
+  constexpr int SB = cls_stage_bytes<DT>();           // stage bytes (the layout of stage_tile)
+  constexpr int HALF = TILE * 4 + 16;                 // float32: offset of the y half
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kClsStages], empty[kClsStages];
   __shared__ int st_tile[kClsStages], st_set[kClsStages], st_head[kClsStages];
   __shared__ uint16_t wq[kClsConsumers][IW * 32];     // pass-2 queue: item << 5 | lane
-  __shared__ uint2 vb[kClsConsumers][IW * 32];         // views (float64) / points (int32) of the warp's slice
+  __shared__ uint2 vb[kClsConsumers][IW * 32];         // views (float64) / points (int32, float32) of the warp's slice
   __shared__ float4 woct[kClsConsumers][OCT ? 8 : 1];  // octagon mode: the edges' FP32 filters, per warp
   __shared__ WarpParams wpar[kClsConsumers];
 
@@ -1142,17 +1259,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
       const SetDesc sd = get_set(j, s);
       const int64_t i0 = (int64_t)(t - sd.tile2) * TILE;
       const int np = (int)min((int64_t)TILE, sd.n - i0);
-      const char* src = reinterpret_cast<const char*>(j.pts) + (sd.off + i0) * PB;
-      unsigned char* dst = smem + slot * SB + 16;
-      const int head = ((uintptr_t)src & 15) ? 1 : 0;       // int32 only
-      const int rem = np - head;
-      const int tail = ((rem * PB) & 15) ? 1 : 0;
-      const uint32_t bytes = (uint32_t)(rem - tail) * PB;
-      st_head[slot] = head;
-      if (head) *reinterpret_cast<P*>(dst - PB) = *reinterpret_cast<const P*>(src);
-      if (tail) *reinterpret_cast<P*>(dst + (np - 1 - head) * PB) = *reinterpret_cast<const P*>(src + (size_t)(np - 1) * PB);
-      mbar_arrive_tx(&full[slot], bytes);
-      if (bytes) tma_load_1d_stream(dst, src + head * PB, bytes, &full[slot]);
+      stage_tile<DT>(j, sd.off + i0, np, smem + slot * SB, HALF, &full[slot], false, &st_head[slot]);
       issued = it + 1;
     }
     if (!ok) {
@@ -1219,7 +1326,11 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
     // this pass and the producer refills it while pass 2 runs.
     uint32_t nim = 0;                              // items that need pass 2
     uint2* vbw = vb[warp];
-    if constexpr (DT == DT_F64) {
+    if constexpr (DT == DT_F32) {
+      const float* vx = reinterpret_cast<const float*>(smem + slot * SB + 16) - (st_head[slot] & 0xFF);
+      const float* vy = reinterpret_cast<const float*>(smem + slot * SB + HALF + 16) - (st_head[slot] >> 8);
+      nim = a2_pass1_f32<OCT, IW>(vx, vy, wb, lane, npv, cp, vbw, woct[warp]);
+    } else if constexpr (DT == DT_F64) {
       nim = shortv ? a2_pass1_f64<true, OCT, IW>(base, wb, lane, npv, cp, vbw, woct[warp])
                    : a2_pass1_f64<false, OCT, IW>(base, wb, lane, npv, cp, vbw, woct[warp]);
     } else {
@@ -1271,7 +1382,9 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
       }
       __syncwarp();
       const int64_t ob = sd.off + t0 + wb;
-      const P* gp = reinterpret_cast<const P*>(j.pts) + sd.off + t0;
+      // float64: exact coordinates from global memory; float32: the views
+      // are the values (widened where needed)
+      const P* gp = DT == DT_F64 ? reinterpret_cast<const P*>(j.pts) + sd.off + t0 : nullptr;
       uint32_t run = 0;
       for (uint32_t e0 = 0; e0 < nq; e0 += 32) {
         const uint32_t e = e0 + lane;
@@ -1284,7 +1397,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
           i = wb + slot_i;
           const uint2 v = vbw[slot_i];
           float X, Y;
-          if constexpr (DT == DT_F64) {
+          if constexpr (DT != DT_I32) {
             X = __uint_as_float(v.x);
             Y = __uint_as_float(v.y);
             const float d0 = __fmaf_rn(cp.fA[0], Y, __fmaf_rn(cp.fB[0], X, cp.fC[0]));
@@ -1298,7 +1411,8 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
             r = !(d1 > cp.fE[1]) ? (d1 < -cp.fE[1] ? 2u : 15u) : r;
             r = !(d0 > cp.fE[0]) ? (d0 < -cp.fE[0] ? 1u : 15u) : r;
             if (r == 15u) {
-              p = gp[i];
+              if constexpr (DT == DT_F32) p = make_double2(widen_f32(X), widen_f32(Y));
+              else p = gp[i];
               r = (uint32_t)region_exact_f64(p.x, p.y, cg.ex, cg.ey, cp.flags);
             }
           } else {
@@ -1320,7 +1434,8 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
           }
           if constexpr (OCT) {
             if (r != 0) {
-              if constexpr (DT == DT_F64) p = gp[i];
+              if constexpr (DT == DT_F32) p = make_double2(widen_f32(X), widen_f32(Y));
+              else if constexpr (DT == DT_F64) p = gp[i];
               if (oct_inside_exact<DT>(woct[warp], cg, X, Y, p)) r = 0;    // inside the octagon
             }
           }
@@ -1329,6 +1444,8 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
             const int bk = stair_bucket(sort_u(X, Y, qr), wp.slo[qr], wp.ssc[qr]);
             if (cmp_view_order(X, Y, qr) > __ldg(pre + qr * kStairB + bk)) r = 0;    // dominated
           }
+          if constexpr (DT == DT_F32)
+            if (r != 0) p = make_double2(widen_f32(X), widen_f32(Y));
         }
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, r != 0);
         if (r != 0) {
@@ -1336,7 +1453,7 @@ __global__ void __launch_bounds__(kClsBlock, 2) k_classify(Job j, Ws w) {
           const int64_t o = ob + run + __popc(b & lt_mask);
           w.keyB[o] = sort_key<DT>(p, (int)r);
           w.valB[o] = ((r - 1u) << 30) | (uint32_t)(t0 + i);
-          if constexpr (DT == DT_F64) w.spvB[o] = spa_v_f64(p.x, p.y, (int)r - 1);
+          if constexpr (DT != DT_I32) w.spvB[o] = spa_v_f64(p.x, p.y, (int)r - 1);
           else w.spvB[o] = spa_v_i32(p.x, p.y, (int)r - 1);
           const uint32_t inc = 1u << (((r - 1u) & 1u) * 16u);
           if (r <= 2u) rc01 += inc; else rc23 += inc;
@@ -1523,6 +1640,9 @@ int extremes_blocks_per_sm(int dtype) {
   if (dtype == DT_F64) {
     extremes_attr<DT_F64, false>();
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_F64, false>, kExtBlock, kExtSmem);
+  } else if (dtype == DT_F32) {
+    extremes_attr<DT_F32, false>();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_F32, false>, kExtBlock, kExtSmem);
   } else {
     extremes_attr<DT_I32, false>();
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extremes<DT_I32, false>, kExtBlock, kExtSmem);
@@ -1542,6 +1662,9 @@ int launch_extremes(const Job& j, const Ws& w, const Launch& L) {
   if (j.dtype == DT_F64) {
     if (oct) launch_extremes_t<DT_F64, true>(j, w, L);
     else launch_extremes_t<DT_F64, false>(j, w, L);
+  } else if (j.dtype == DT_F32) {
+    if (oct) launch_extremes_t<DT_F32, true>(j, w, L);
+    else launch_extremes_t<DT_F32, false>(j, w, L);
   } else {
     if (oct) launch_extremes_t<DT_I32, true>(j, w, L);
     else launch_extremes_t<DT_I32, false>(j, w, L);
@@ -1552,6 +1675,7 @@ int launch_extremes(const Job& j, const Ws& w, const Launch& L) {
 int launch_stairs(const Job& j, const Ws& w, const Launch& L) {
   if (j.nchunk3 == 0) return 0;
   if (j.dtype == DT_F64) launch_pdl(k_stairs<DT_F64>, j.nchunk3, kThreads, 0, L.stream, j, w);
+  else if (j.dtype == DT_F32) launch_pdl(k_stairs<DT_F32>, j.nchunk3, kThreads, 0, L.stream, j, w);
   else launch_pdl(k_stairs<DT_I32>, j.nchunk3, kThreads, 0, L.stream, j, w);
   return 1;
 }
@@ -1578,6 +1702,9 @@ int launch_classify(const Job& j, const Ws& w, const Launch& L) {
   if (j.dtype == DT_F64) {
     if (oct) launch_classify_t<DT_F64, true>(j, w, L, grid);
     else launch_classify_t<DT_F64, false>(j, w, L, grid);
+  } else if (j.dtype == DT_F32) {
+    if (oct) launch_classify_t<DT_F32, true>(j, w, L, grid);
+    else launch_classify_t<DT_F32, false>(j, w, L, grid);
   } else {
     if (oct) launch_classify_t<DT_I32, true>(j, w, L, grid);
     else launch_classify_t<DT_I32, false>(j, w, L, grid);

@@ -692,7 +692,7 @@ int launch_small(const Job& j, const Ws& w, const Launch& L) {
   int cap = L.grid_cap / 4;            // one 512-thread CTA per SM
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  if (j.dtype == DT_F64) {
+  if (j.dtype != DT_I32) {   // float32 input: the float64 stages
     static bool once = [] {
       cudaFuncSetAttribute(k_small<DT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmSmem);
       return true;

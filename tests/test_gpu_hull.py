@@ -307,6 +307,43 @@ def test_f32soa_special_values_and_unaligned_vectors():
     assert np.array_equal(got, oracle.hull(base[1:].astype(np.float64)))
 
 
+def test_f32soa_tiny_sets():
+    """1..12 float32 points, mixed signs: tiles that the plain loads fill
+    alone (no bulk bytes), or nearly so."""
+    rng = np.random.default_rng(31)
+    for t in range(240):
+        n = 1 + t % 12
+        p = (rng.random((n, 2)) * 2 - 1).astype(np.float32)
+        if t % 3 == 0:
+            p = np.abs(p)
+        check_f32(p)
+
+
+@pytest.mark.parametrize("n", [5, 4095, 4097, 70_001])
+def test_f32soa_every_vector_alignment(n):
+    """x and y starting 0..3 floats past a 16-byte boundary, independently:
+    the tiles' leading and trailing points of each vector that the bulk
+    copies cannot take."""
+    base = inputs.disk_f64(n + 3, n % 13).astype(np.float32)
+    bx = torch.from_numpy(np.ascontiguousarray(base[:, 0])).to(DEV)
+    by = torch.from_numpy(np.ascontiguousarray(base[:, 1])).to(DEV)
+    for ox in range(4):
+        for oy in range(4):
+            got = cch.hull_f32soa(bx[ox:ox + n], by[oy:oy + n]).cpu().numpy()
+            q = np.stack([base[ox:ox + n, 0], base[oy:oy + n, 1]], axis=1).astype(np.float64)
+            assert np.array_equal(got, oracle.hull(q)), (n, ox, oy)
+
+
+def test_f32soa_multiblock_sort_path():
+    """A float32 circle: about n / 4 round-1 survivors in every region, far
+    above the shared-memory sort's limit, so the multi-block sort and SPA
+    read the float32 vectors."""
+    n = 300_000
+    t = 2 * np.pi * np.arange(n) / n
+    p = np.stack([np.cos(t), np.sin(t)], axis=1).astype(np.float32)
+    check_f32(p[np.random.default_rng(4).permutation(n)])
+
+
 def test_f32soa_nonfinite_is_reported():
     p = inputs.square_f64(5000, 3).astype(np.float32)
     for bad in (np.nan, np.inf, -np.inf):
