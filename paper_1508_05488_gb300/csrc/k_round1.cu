@@ -507,6 +507,19 @@ __device__ __forceinline__ void oct_update(uint64_t dq[4], float X, float Y, uin
   dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | i);
 }
 
+// Minimum / maximum that return NaN when either operand is NaN, so that a
+// NaN coordinate shows up in a lane's running extremes.
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+  float d;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float d;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+
 template <int DT, bool OCT>
 __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   griddep_enter();
@@ -604,8 +617,78 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     const int np = (int)min((int64_t)TILE, sd.n - t0);
     const unsigned char* base = smem + slot * SB + 16 - st_head[slot] * PB;
     const int wb = warp * WPTS;
-    if constexpr (DT == DT_F32) {
-      // exact 32-bit keys of the two vectors, as for int32
+    if constexpr (!OCT && DT != DT_I32) {
+      // Each lane first folds its items into running FP32 extremes (float64:
+      // the top word read as FP32, the order of the filter below; float32:
+      // the values), plus the smallest top-word magnitude (float64).  Only a
+      // warp in which some lane's extremes reach the running bounds (ties and
+      // NaN included), or in which a magnitude is tiny, rescans its items
+      // with the exact keys: after the first tiles that is rare, so most
+      // points cost one load and four min / max operations.
+      const float* vx = reinterpret_cast<const float*>(smem + slot * SB + 16) - (st_head[slot] & 0xFF);
+      const float* vy = reinterpret_cast<const float*>(smem + slot * SB + HALF + 16) - (st_head[slot] >> 8);
+      const float inf = __int_as_float(0x7F800000);
+      float mnx = inf, mny = inf, mxx = -inf, mxy = -inf, tmn = inf;
+#pragma unroll
+      for (int k = 0; k < IW; k++) {
+        const int i = wb + k * 32 + lane;
+        if (i < np) {
+          float fx, fy;
+          if constexpr (DT == DT_F64) {
+            const uint4 q = *reinterpret_cast<const uint4*>(base + i * PB);
+            fx = __uint_as_float(q.y);
+            fy = __uint_as_float(q.w);
+            tmn = fmin_nan(tmn, fmin_nan(fabsf(fx), fabsf(fy)));
+          } else {
+            fx = vx[i];
+            fy = vy[i];
+          }
+          mnx = fmin_nan(mnx, fx);
+          mny = fmin_nan(mny, fy);
+          mxx = fmax_nan(mxx, fx);
+          mxy = fmax_nan(mxy, fy);
+        }
+      }
+      bool rare = !(mnx > thf[0]) | !(mny > thf[1]) | !(mxx < thf[2]) | !(mxy < thf[3]);
+      if constexpr (DT == DT_F64) rare |= !(tmn >= kTinyTopF);
+      if (__any_sync(0xFFFFFFFFu, rare)) {
+        // the stage is still held: rescan the items
+#pragma unroll 1
+        for (int k = 0; k < IW; k++) {
+          const int i = wb + k * 32 + lane;
+          if (i >= np) continue;
+          if constexpr (DT == DT_F64) {
+            const uint4 q = *reinterpret_cast<const uint4*>(base + i * PB);
+            const float fx = __uint_as_float(q.y), fy = __uint_as_float(q.w);
+            if ((fabsf(fx) < kTinyTopF) | (fabsf(fy) < kTinyTopF)) {
+              // zeros and tiny magnitudes: the exact lower end of the domain check
+              uint32_t a = q.y & 0x7FFFFFFFu;
+              if ((a | q.x) != 0) amin = min(amin, a);
+              lomag = min(lomag, a);
+              a = q.w & 0x7FFFFFFFu;
+              if ((a | q.z) != 0) amin = min(amin, a);
+              lomag = min(lomag, a);
+            }
+            if (!(fx > thf[0]) | !(fy > thf[1]) | !(fx < thf[2]) | !(fy < thf[3])) {
+              uint32_t kxh, kxl, kyh, kyl, dummy = 0;
+              f64_key_words(((uint64_t)q.y << 32) | q.x, kxh, kxl, dummy);
+              f64_key_words(((uint64_t)q.w << 32) | q.z, kyh, kyl, dummy);
+              a1_update<DT>(kxh, kxl, kyh, kyl, i0 + (uint32_t)i, best);
+            }
+          } else {
+            const float X = vx[i], Y = vy[i];
+            if (!(X > thf[0]) | !(Y > thf[1]) | !(X < thf[2]) | !(Y < thf[3]))
+              a1_update<DT>(key_f32(X), 0u, key_f32(Y), 0u, i0 + (uint32_t)i, best);
+          }
+        }
+        a1_thresholds_f(best, thf);
+      }
+      __syncwarp();
+      if (lane == 0)   // the warp is done with the stage: release it to the producer
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[slot])) : "memory");
+      continue;
+    } else if constexpr (DT == DT_F32) {
+      // octagon mode: exact 32-bit keys of the two vectors, as for int32
       const float* vx = reinterpret_cast<const float*>(smem + slot * SB + 16) - (st_head[slot] & 0xFF);
       const float* vy = reinterpret_cast<const float*>(smem + slot * SB + HALF + 16) - (st_head[slot] >> 8);
       uint32_t xh[IW], yh[IW];
