@@ -37,6 +37,16 @@
 //  the records come back into shared memory in one sequential copy, and
 //  steps 2a and 3 read only shared memory; the output gathers only the
 //  survivors' point indices.
+//  Cluster form (CL = 8 CTAs per (set, region), for calls of a few sets, on
+//  regions of at least kSplitMin candidates; smaller regions are left to the
+//  leader CTA alone): every CTA of the cluster builds the two tables over
+//  its own slice of the candidates, the copies are merged through distributed
+//  shared memory (each CTA takes the minimum of one slice of the words over
+//  the eight copies and writes it back to all of them), and every CTA takes
+//  the prefix minima and runs the keep test on its slice, listing its kept
+//  candidates, their bucket counts and index-order bits in the leader's
+//  shared memory.  The leader then sorts and scans as above.
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "cch_internal.cuh"
@@ -50,6 +60,9 @@ constexpr int kFineB = 16384;                      // fine buckets of the sort k
 constexpr int kFineB2 = 8192;                      // fine buckets of the SPA value per region
 constexpr int kOccMax = 32;                        // largest bucket the counting path ranks
 constexpr int kRecMax = 4096;                      // most kept candidates the record path holds
+constexpr int kSmCluster = 8;                      // CTAs per (set, region) in the cluster form
+constexpr int kSmClusterSets = 4;                  // calls of at most this many sets take the cluster form
+constexpr uint32_t kSplitMin = 4096;               // smallest region the cluster splits
 // Dynamic shared memory, overlays of one 200 KB block (tables padded by one
 // word in 32):
 //   filter         table A u32 | table B u32 | kept-candidate list u16 (its
@@ -216,9 +229,10 @@ __device__ __forceinline__ void prefix_min_excl(uint32_t* t, uint32_t seed, uint
   }
 }
 
-template <int DT>
+template <int DT, int CL>
 __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
   griddep_enter();
+  namespace cg = cooperative_groups;
   using P = typename std::conditional<DT == DT_F64, double2, int2>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* vminA = reinterpret_cast<uint32_t*>(smem);                           // table A (padded)
@@ -240,8 +254,21 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t total = w.ctr[CT_SMALL_TOTAL];
+  const uint32_t rank = blockIdx.x % CL;           // CTA within the cluster (clusters are consecutive CTAs)
+  // the leader's lists (this CTA's own without a cluster)
+  uint16_t* klistL = klist;
+  uint32_t* bcntL = bcnt;
+  uint32_t* keepwL = keepw;
+  uint32_t* nkL = &sh_nk;
+  if constexpr (CL > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    klistL = cl.map_shared_rank(klist, 0);
+    bcntL = cl.map_shared_rank(bcnt, 0);
+    keepwL = cl.map_shared_rank(keepw, 0);
+    nkL = cl.map_shared_rank(&sh_nk, 0);
+  }
 
-  for (uint32_t q = blockIdx.x; q < total; q += gridDim.x) {
+  for (uint32_t q = blockIdx.x / CL; q < total; q += gridDim.x / CL) {
     const uint32_t g = w.small_seg[q];
     const int s = (int)(g >> 2), r = (int)(g & 3);
     const SetDesc sd = get_set(j, s);
@@ -262,6 +289,13 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
       }
     }
     const uint64_t v0 = spa_value_of<DT>(e, r);
+    // this CTA's candidates [lo, hi) (all of them without a cluster, or on a
+    // region the cluster does not split -- the same decision in every CTA);
+    // the slices start on multiples of 32 (one keepw word per warp and step)
+    const bool split = CL > 1 && m >= kSplitMin;
+    if (CL > 1 && !split && rank != 0) continue;
+    const uint32_t chunk = split ? (m + CL * 32 - 1) / (CL * 32) * 32 : m;
+    const uint32_t lo = min(m, rank * chunk), hi = min(m, lo + chunk);
 
     // ---- 1. fine dominance filter ------------------------------------
     // Table A: buckets of the sort key (every candidate's key lies between
@@ -278,28 +312,58 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
       fb.init<DT>(spa_value_of<DT>(e1, r), v0, fp, r == 1 || r == 2);
     }
     for (int i = tid; i < kPadA + kPadB; i += kSmThreads) vminA[i] = 0xFFFFFFFFu;
-    for (int i = tid; i < kPadC; i += kSmThreads) bcnt[i] = 0u;
-    for (int i = tid; i < kSmallMax / 32; i += kSmThreads) keepw[i] = 0u;
-    if (tid == 0) sh_nk = 0;
-    __syncthreads();
+    if (rank == 0) {
+      for (int i = tid; i < kPadC; i += kSmThreads) bcnt[i] = 0u;
+      for (int i = tid; i < kSmallMax / 32; i += kSmThreads) keepw[i] = 0u;
+      if (tid == 0) sh_nk = 0;
+    }
+    if (split) cg::this_cluster().sync();   // the leader's tables and lists are clear
+    else __syncthreads();
 #pragma unroll 1
-    for (uint32_t i0 = 0; i0 < m; i0 += kSmThreads * 8) {
+    for (uint32_t i0 = lo; i0 < hi; i0 += kSmThreads * 8) {
       uint64_t kk[8], va[8];
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const uint32_t i = i0 + u * kSmThreads + tid;
-        kk[u] = i < m ? kin[i] : 0ull;
-        va[u] = i < m ? vv[i] : 0ull;
+        kk[u] = i < hi ? kin[i] : 0ull;
+        va[u] = i < hi ? vv[i] : 0ull;
       }
 #pragma unroll
       for (int u = 0; u < 8; u++) {
-        if (i0 + u * kSmThreads + tid < m) {
+        if (i0 + u * kSmThreads + tid < hi) {
           atomicMin(&vminA[pad32(fa.bucket<DT>(kk[u]))], key_hi<DT>(va[u]));
           atomicMin(&vminB[pad32(fb.bucket<DT>(va[u]))], key_hi<DT>(kk[u]));
         }
       }
     }
-    __syncthreads();
+    if (split) {
+      // merge the cluster's tables: this CTA takes words [w0, w1) of the
+      // (contiguous) two tables, minimum over the eight copies, written back
+      // to every copy (two words a step, their remote loads in flight together)
+      cg::cluster_group cl = cg::this_cluster();
+      cl.sync();
+      constexpr uint32_t W = kPadA + kPadB, S = (W + CL - 1) / CL;
+      const uint32_t w0 = rank * S, w1 = min(W, w0 + S);
+      for (uint32_t x = w0 + tid; x < w1; x += 2 * kSmThreads) {
+        const uint32_t x2 = x + kSmThreads;
+        uint32_t v[CL], v2[CL];
+#pragma unroll
+        for (int c = 0; c < CL; c++) {
+          v[c] = cl.map_shared_rank(vminA, c)[x];
+          v2[c] = x2 < w1 ? cl.map_shared_rank(vminA, c)[x2] : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int c = 1; c < CL; c++) { v[0] = min(v[0], v[c]); v2[0] = min(v2[0], v2[c]); }
+#pragma unroll
+        for (int c = 0; c < CL; c++) {
+          cl.map_shared_rank(vminA, c)[x] = v[0];
+          if (x2 < w1) cl.map_shared_rank(vminA, c)[x2] = v2[0];
+        }
+      }
+      cl.sync();
+    } else {
+      __syncthreads();
+    }
     // exclusive prefix minima over the buckets; table A is seeded with E_r
     prefix_min_excl<kFineB / kSmThreads>(vminA, key_hi<DT>(v0), wsum);
     __syncthreads();
@@ -312,20 +376,20 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
     uint64_t* rvG = w.spvB + sd.off + rbase;
     uint32_t* riG = w.valB + sd.off + rbase;
 #pragma unroll 1
-    for (uint32_t i0 = 0; i0 < m; i0 += kSmThreads * 8) {
+    for (uint32_t i0 = lo; i0 < hi; i0 += kSmThreads * 8) {
       uint64_t kk[8], va[8];
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const uint32_t i = i0 + u * kSmThreads + tid;
-        kk[u] = i < m ? kin[i] : 0ull;
-        va[u] = i < m ? vv[i] : 0ull;
+        kk[u] = i < hi ? kin[i] : 0ull;
+        va[u] = i < hi ? vv[i] : 0ull;
       }
 #pragma unroll
       for (int u = 0; u < 8; u++) {
         const uint32_t i = i0 + u * kSmThreads + tid;
         bool keep = false;
         uint32_t b = 0;
-        if (i < m) {
+        if (i < hi) {
           b = fa.bucket<DT>(kk[u]);
           keep = key_hi<DT>(va[u]) <= vminA[pad32(b)] &&
                  key_hi<DT>(kk[u]) <= vminB[pad32(fb.bucket<DT>(va[u]))];
@@ -334,20 +398,25 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
         if (bal) {
           uint32_t base = 0;
           if (lane == 0) {
-            keepw[(i0 + u * kSmThreads) / 32 + warp] = bal;
-            base = atomicAdd(&sh_nk, (uint32_t)__popc(bal));
+            keepwL[(i0 + u * kSmThreads) / 32 + warp] = bal;
+            base = atomicAdd(nkL, (uint32_t)__popc(bal));
           }
           base = __shfl_sync(0xFFFFFFFFu, base, 0);
           if (keep) {
             const uint32_t pos = base + __popc(bal & lt_mask);
-            klist[pos] = (uint16_t)i;
-            atomicAdd(&bcnt[pad32(b >> 1)], 1u << ((b & 1u) * 16u));
+            klistL[pos] = (uint16_t)i;
+            atomicAdd(&bcntL[pad32(b >> 1)], 1u << ((b & 1u) * 16u));
             if (pos < kRecMax) { rkG[pos] = kk[u]; rvG[pos] = va[u]; riG[pos] = i; }
           }
         }
       }
     }
-    __syncthreads();
+    if (split) {
+      cg::this_cluster().sync();      // every kept candidate is listed at the leader
+      if (rank != 0) continue;        // the leader sorts and scans
+    } else {
+      __syncthreads();
+    }
     // exclusive scan of the bucket counts into bucket starts (in place, u16)
     uint32_t m2 = 0, maxocc = 0;
     {
@@ -687,26 +756,76 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
   }
 }
 
-int launch_small(const Job& j, const Ws& w, const Launch& L) {
-  int grid = 4 * j.nsets;
-  int cap = L.grid_cap / 4;            // one 512-thread CTA per SM
+template <int DT, int CL>
+static void small_attr() {
+  static bool once = [] {
+    cudaFuncSetAttribute(k_small<DT, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmSmem);
+    return true;
+  }();
+  (void)once;
+}
+
+// Clusters of kSmCluster CTAs that fit at once (0: none, or the query failed).
+template <int DT>
+static int small_clusters_resident() {
+  static int n = [] {
+    small_attr<DT, kSmCluster>();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kSmCluster * 64);
+    cfg.blockDim = dim3(kSmThreads);
+    cfg.dynamicSmemBytes = kSmSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSmCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, k_small<DT, kSmCluster>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      c = 0;
+    }
+    return c;
+  }();
+  return n;
+}
+
+template <int DT>
+static void launch_small_t(const Job& j, const Ws& w, const Launch& L) {
+  const int segs = 4 * j.nsets;
+  const int ncl = j.nsets <= kSmClusterSets ? small_clusters_resident<DT>() : 0;
+  if (ncl > 0) {
+    small_attr<DT, kSmCluster>();
+    const int nc = segs < ncl ? segs : ncl;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc * kSmCluster);
+    cfg.blockDim = dim3(kSmThreads);
+    cfg.dynamicSmemBytes = kSmSmem;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = kSmCluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    cudaLaunchKernelEx(&cfg, k_small<DT, kSmCluster>, j, w);
+    return;
+  }
+  int grid = segs;
+  const int cap = L.grid_cap / 4;      // one 512-thread CTA per SM
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  if (j.dtype != DT_I32) {   // float32 input: the float64 stages
-    static bool once = [] {
-      cudaFuncSetAttribute(k_small<DT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmSmem);
-      return true;
-    }();
-    (void)once;
-    launch_pdl(k_small<DT_F64>, grid, kSmThreads, kSmSmem, L.stream, j, w);
-  } else {
-    static bool once = [] {
-      cudaFuncSetAttribute(k_small<DT_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmSmem);
-      return true;
-    }();
-    (void)once;
-    launch_pdl(k_small<DT_I32>, grid, kSmThreads, kSmSmem, L.stream, j, w);
-  }
+  small_attr<DT, 1>();
+  launch_pdl(k_small<DT, 1>, grid, kSmThreads, kSmSmem, L.stream, j, w);
+}
+
+int launch_small(const Job& j, const Ws& w, const Launch& L) {
+  if (j.dtype != DT_I32) launch_small_t<DT_F64>(j, w, L);   // float32 input: the float64 stages
+  else launch_small_t<DT_I32>(j, w, L);
   return 1;
 }
 
