@@ -303,22 +303,39 @@ __device__ void edge_filter(double ax, double ay, double bx, double by, double x
   }
 }
 
-// Edge set-up of one set, run by one thread once E1..E4 are known.
+// Edge set-up of one set once E1..E4 are known, run by one warp (every lane
+// holds the set's extremes): lane k < 4 loads E_k, sets up edge k (octagon
+// mode: finds D_k, and lane k < 8 sets up octagon edge k) and region k's
+// stairs range; the flags, the same in every lane, are written by lane 0.
 template <int DT>
-__device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, const Lex best[4],
-                          uint32_t amin, uint32_t lomag, const uint64_t* dq) {
+__device__ void setup_set_warp(const Job& j, const Ws& w, int s, const SetDesc& sd, const Lex best[4],
+                               uint32_t amin, uint32_t lomag, const uint64_t* dq) {
   SetCtl& c = w.ctl[s];
   using P = typename PointT<DT>::T;
-  uint32_t flags = 0;
+  const int lane = threadIdx.x & 31;
+  const int k1 = (lane + 1) & 3;
+  const uint32_t myidx = lane == 0 ? best[0].idx : lane == 1 ? best[1].idx : lane == 2 ? best[2].idx : best[3].idx;
+  P my{};
+  if (lane < 4) my = input_point<P>(j, sd.off + myidx);
   P e[4];
+#pragma unroll
   for (int k = 0; k < 4; k++) {
-    c.ek1[k] = best[k].k1;
-    c.ek2[k] = best[k].k2;
-    c.eidx[k] = best[k].idx;
-    e[k] = input_point<P>(j, sd.off + best[k].idx);
-    c.ex[k] = (double)e[k].x;
-    c.ey[k] = (double)e[k].y;
+    e[k].x = __shfl_sync(0xFFFFFFFFu, my.x, k);
+    e[k].y = __shfl_sync(0xFFFFFFFFu, my.y, k);
   }
+  P nb;                                    // E_{k+1} on lane k
+  nb.x = __shfl_sync(0xFFFFFFFFu, my.x, k1);
+  nb.y = __shfl_sync(0xFFFFFFFFu, my.y, k1);
+  if (lane == 0) {
+    for (int k = 0; k < 4; k++) {
+      c.ek1[k] = best[k].k1;
+      c.ek2[k] = best[k].k2;
+      c.eidx[k] = best[k].idx;
+      c.ex[k] = (double)e[k].x;
+      c.ey[k] = (double)e[k].y;
+    }
+  }
+  uint32_t flags = 0;
   if constexpr (DT != DT_I32) {
     // NaN, Inf and huge values sort beyond every finite value, so they show
     // up among the extremes; tiny nonzero values were folded into amin.
@@ -332,16 +349,19 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
       }
     }
     if (st == 0 && amin < ((1023u - 400u) << 20)) st = ST_RANGE;
-    if (st) { c.status = st; return; }
+    if (st) {
+      if (lane == 0) c.status = st;
+      return;
+    }
   }
   for (int k = 0; k < 4; k++)
-    if (c.eidx[k] == c.eidx[(k + 1) & 3]) flags |= SF_DEGEN0 << k;
+    if (best[k].idx == best[(k + 1) & 3].idx) flags |= SF_DEGEN0 << k;
   bool small = true;
   // E1 = P_minx, E3 = P_maxx, E2 = P_miny, E4 = P_maxy
-  const double xm = fmax(fabs(c.ex[0]), fabs(c.ex[2]));
-  const double ym = fmax(fabs(c.ey[1]), fabs(c.ey[3]));
+  const double xm = fmax(fabs((double)e[0].x), fabs((double)e[2].x));
+  const double ym = fmax(fabs((double)e[1].y), fabs((double)e[3].y));
   if constexpr (DT == DT_I32) {
-    double spanx = c.ex[2] - c.ex[0], spany = c.ey[3] - c.ey[1];
+    double spanx = (double)e[2].x - (double)e[0].x, spany = (double)e[3].y - (double)e[1].y;
     if (spanx >= 2147483648.0 || spany >= 2147483648.0) flags |= SF_WIDE;
   } else {
     const double lim = 1152921504606846976.0;  // 2^60
@@ -351,64 +371,71 @@ __device__ void setup_set(const Job& j, const Ws& w, int s, const SetDesc& sd, c
     // (f32_view_short) equals f64_trunc_f32
     if (DT == DT_F64 && small && lomag >= kTinyTopBits) flags |= SF_SHORTVIEW;
   }
-  {
-    const bool filt = small && !(j.opts & OPT_NO_FILTER);
-    if (filt) flags |= SF_FILTER;
-    // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
-    // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on the
-    // FP32 views X, Y (float64: significand-truncated, |X - x| < 2^-23 |x|;
-    // int32: rounded to nearest, |X - x| <= 2^-24 |x|; float32: exact) differs from the exact
-    // value by at most 5.01 u (|A| Ymax + |B| Xmax + |B||ax| + |A||ay|) plus
-    // underflow terms, u = 2^-24; E below uses 6 u and rounds up.  Without
-    // the filter every point takes the exact path (E = inf); a degenerate
-    // edge is always "inside" (A = B = 0, C = 1, E = 0).
-    for (int k = 0; k < 4; k++) {
-      const int k1 = (k + 1) & 3;
-      edge_filter(c.ex[k], c.ey[k], c.ex[k1], c.ey[k1], xm, ym, filt, c.fA[k], c.fB[k], c.fC[k], c.fE[k]);
-    }
-    if (dq) {
-      // Octagon (OPT_OCTAGON): vertex 2r is E_r, vertex 2r+1 the diagonal
-      // extreme D_r when it lies strictly outside edge r (exact test), else
-      // E_{r+1} (the edge D_r -> E_{r+1} is then degenerate).  Each kept D_r
-      // is the extreme of its direction among the set's FP32 scores, so the
-      // eight vertices in this order form a convex polygon inside the hull.
-      for (int r = 0; r < 4; r++) {
-        const int r1 = (r + 1) & 3;
-        c.ovx[2 * r] = c.ex[r];
-        c.ovy[2 * r] = c.ey[r];
-        c.didx[r] = -1;
-        double dx = c.ex[r1], dy = c.ey[r1];
-        if (!(flags & (SF_DEGEN0 << r)) && dq[r] != ~0ull) {
-          const uint32_t di = (uint32_t)dq[r];
-          const P d = input_point<P>(j, sd.off + di);
-          int o;
-          if constexpr (DT != DT_I32) o = orient_f64(c.ex[r], c.ey[r], c.ex[r1], c.ey[r1], d.x, d.y);
-          else o = orient_i32((int)c.ex[r], (int)c.ey[r], (int)c.ex[r1], (int)c.ey[r1], d.x, d.y, true);
-          if (o < 0) { dx = (double)d.x; dy = (double)d.y; c.didx[r] = (int32_t)di; }
-        }
-        c.ovx[2 * r + 1] = dx;
-        c.ovy[2 * r + 1] = dy;
+  const bool filt = small && !(j.opts & OPT_NO_FILTER);
+  if (filt) flags |= SF_FILTER;
+  // orient(a, b, p) = A py - B px + C with A = bx-ax, B = by-ay,
+  // C = B ax - A ay.  The FP32 evaluation fma(A, Y, fma(-B, X, C)) on the
+  // FP32 views X, Y (float64: significand-truncated, |X - x| < 2^-23 |x|;
+  // int32: rounded to nearest, |X - x| <= 2^-24 |x|; float32: exact)
+  // differs from the exact value by at most 5.01 u (|A| Ymax + |B| Xmax +
+  // |B||ax| + |A||ay|) plus underflow terms, u = 2^-24; E below uses 6 u and
+  // rounds up.  Without the filter every point takes the exact path
+  // (E = inf); a degenerate edge is always "inside" (A = B = 0, C = 1, E = 0).
+  if (lane < 4)
+    edge_filter((double)my.x, (double)my.y, (double)nb.x, (double)nb.y, xm, ym, filt, c.fA[lane], c.fB[lane],
+                c.fC[lane], c.fE[lane]);
+  if (dq) {
+    // Octagon (OPT_OCTAGON): vertex 2r is E_r, vertex 2r+1 the diagonal
+    // extreme D_r when it lies strictly outside edge r (exact test), else
+    // E_{r+1} (the edge D_r -> E_{r+1} is then degenerate).  Each kept D_r
+    // is the extreme of its direction among the set's FP32 scores, so the
+    // eight vertices in this order form a convex polygon inside the hull.
+    double dx = (double)nb.x, dy = (double)nb.y;
+    if (lane < 4) {
+      const uint64_t dqr = dq[lane];
+      int32_t didx = -1;
+      if (!(flags & (SF_DEGEN0 << lane)) && dqr != ~0ull) {
+        const uint32_t di = (uint32_t)dqr;
+        const P d = input_point<P>(j, sd.off + di);
+        int o;
+        if constexpr (DT != DT_I32) o = orient_f64((double)my.x, (double)my.y, (double)nb.x, (double)nb.y, d.x, d.y);
+        else o = orient_i32(my.x, my.y, nb.x, nb.y, d.x, d.y, true);
+        if (o < 0) { dx = (double)d.x; dy = (double)d.y; didx = (int32_t)di; }
       }
-      for (int k = 0; k < 8; k++) {
-        const int k1 = (k + 1) & 7;
-        edge_filter(c.ovx[k], c.ovy[k], c.ovx[k1], c.ovy[k1], xm, ym, filt, c.oA[k], c.oB[k], c.oC[k], c.oE[k]);
-      }
+      c.ovx[2 * lane] = (double)my.x;
+      c.ovy[2 * lane] = (double)my.y;
+      c.ovx[2 * lane + 1] = dx;
+      c.ovy[2 * lane + 1] = dy;
+      c.didx[lane] = didx;
     }
+    // octagon edge k on lane k < 8: vertices k and k + 1 (vertex v is E_{v/2}
+    // for even v, lane (v-1)/2's D for odd v)
+    const int v0 = lane & 7, v1 = (lane + 1) & 7;
+    const double ex0 = __shfl_sync(0xFFFFFFFFu, (double)my.x, v0 >> 1), ey0 = __shfl_sync(0xFFFFFFFFu, (double)my.y, v0 >> 1);
+    const double dx0 = __shfl_sync(0xFFFFFFFFu, dx, v0 >> 1), dy0 = __shfl_sync(0xFFFFFFFFu, dy, v0 >> 1);
+    const double ex1 = __shfl_sync(0xFFFFFFFFu, (double)my.x, v1 >> 1), ey1 = __shfl_sync(0xFFFFFFFFu, (double)my.y, v1 >> 1);
+    const double dx1 = __shfl_sync(0xFFFFFFFFu, dx, v1 >> 1), dy1 = __shfl_sync(0xFFFFFFFFu, dy, v1 >> 1);
+    if (lane < 8)
+      edge_filter((v0 & 1) ? dx0 : ex0, (v0 & 1) ? dy0 : ey0, (v1 & 1) ? dx1 : ex1, (v1 & 1) ? dy1 : ey1, xm, ym,
+                  filt, c.oA[lane], c.oB[lane], c.oC[lane], c.oE[lane]);
   }
   if (small && !(j.opts & OPT_NO_PREFILTER)) {
     flags |= SF_STAIRS;
-    float X[4], Y[4];
-    for (int k = 0; k < 4; k++) view_at<DT>(j, sd.off + best[k].idx, X[k], Y[k]);
-    // region r runs from E_r to E_{r+1} along its sort coordinate
-    for (int r = 0; r < 4; r++) {
-      int r1 = (r + 1) & 3;
-      float lo = sort_u(X[r], Y[r], r), hi = sort_u(X[r1], Y[r1], r);
-      c.slo[r] = lo;
-      c.shi[r] = hi;
-      c.sscale[r] = hi > lo ? (float)kStairB / (hi - lo) : 0.f;
+    float X = 0.f, Y = 0.f;
+    if (lane < 4) {
+      if constexpr (DT == DT_F32) view_at<DT>(j, sd.off + myidx, X, Y);
+      else f32_view<DT>(my, X, Y);
+    }
+    const float Xn = __shfl_sync(0xFFFFFFFFu, X, k1), Yn = __shfl_sync(0xFFFFFFFFu, Y, k1);
+    // region r (lane r) runs from E_r to E_{r+1} along its sort coordinate
+    if (lane < 4) {
+      const float lo = sort_u(X, Y, lane), hi = sort_u(Xn, Yn, lane);
+      c.slo[lane] = lo;
+      c.shi[lane] = hi;
+      c.sscale[lane] = hi > lo ? (float)kStairB / (hi - lo) : 0.f;
     }
   }
-  c.flags = flags;
+  if (lane == 0) c.flags = flags;
 }
 
 constexpr int kExtStages = 3;                          // TMA ring depth of a1
@@ -846,13 +873,10 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   consumers_sync();
   if (!last) return;
 
-  // Last chunk of the set: reduce the set's partials, clear its sort
-  // histogram and stairs table, set up its edges.
+  // Last chunk of the set: reduce the set's partials, then warp 0 sets up
+  // the set's edges while the other warps clear its sort histogram and
+  // stairs table.
   __threadfence();
-  uint32_t* hist = w.hist + (size_t)s * kSortPasses * 256;
-  for (int i = threadIdx.x; i < kSortPasses * 256; i += kClsConsumers * 32) hist[i] = 0;
-  uint32_t* stt = w.stairs + (size_t)s * 4 * kStairB;
-  for (int i = threadIdx.x; i < 4 * kStairB; i += kClsConsumers * 32) stt[i] = 0xFFFFFFFFu;
 #pragma unroll
   for (int k = 0; k < 4; k++) { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
   amin = 0x7FFFFFFFu;
@@ -890,14 +914,35 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     for (int q = 0; q < 4; q++) red_dq[warp][q] = dqm[q];
   }
   consumers_sync();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < kClsConsumers; q++) {
-      for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
-      amin = min(amin, red_amin[q]);
-      lomag = min(lomag, red_lomag[q]);
-      for (int k = 0; k < 4; k++) dqm[k] = min(dqm[k], red_dq[q][k]);
+  if (warp == 0) {
+    // the eight warps' results, reduced so that every lane holds the set's
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (lane < kClsConsumers) best[k] = red[lane][k];
+      else { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
     }
-    setup_set<DT>(j, w, s, sd, best, amin, lomag, OCT ? dqm : nullptr);
+    amin = lane < kClsConsumers ? red_amin[lane] : 0x7FFFFFFFu;
+    lomag = lane < kClsConsumers ? red_lomag[lane] : 0x7FFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < 4; q++) dqm[q] = lane < kClsConsumers ? red_dq[lane][q] : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
+      amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
+      lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
+      if constexpr (OCT) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) dqm[q] = min(dqm[q], __shfl_xor_sync(0xFFFFFFFFu, dqm[q], o));
+      }
+    }
+    setup_set_warp<DT>(j, w, s, sd, best, amin, lomag, OCT ? dqm : nullptr);
+  } else {
+    const int t = threadIdx.x - 32, nt = (kClsConsumers - 1) * 32;
+    uint32_t* hist = w.hist + (size_t)s * kSortPasses * 256;
+    for (int i = t; i < kSortPasses * 256; i += nt) hist[i] = 0;
+    uint32_t* stt = w.stairs + (size_t)s * 4 * kStairB;
+    for (int i = t; i < 4 * kStairB; i += nt) stt[i] = 0xFFFFFFFFu;
   }
 }
 
