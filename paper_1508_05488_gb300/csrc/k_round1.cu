@@ -993,9 +993,12 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   const SetDesc sd = get_set(j, s);
   const SetCtl& c = w.ctl[s];
   if (c.status != 0 || !(c.flags & SF_STAIRS)) return;   // uniform; table unused
-  float lo[4], hi[4], sc[4];
+  float lo[4], hi[4], sc[4], fa[4], fb[4], fc[4], fe[4];
 #pragma unroll
-  for (int r = 0; r < 4; r++) { lo[r] = c.slo[r]; hi[r] = c.shi[r]; sc[r] = c.sscale[r]; }
+  for (int r = 0; r < 4; r++) {
+    lo[r] = c.slo[r]; hi[r] = c.shi[r]; sc[r] = c.sscale[r];
+    fa[r] = c.fA[r]; fb[r] = -c.fB[r]; fc[r] = c.fC[r]; fe[r] = c.fE[r];
+  }
   for (int i = threadIdx.x; i < 4 * kTb; i += kThreads) (&tb[0][0])[i] = 0xFFFFFFFFu;
   __syncthreads();
 
@@ -1022,10 +1025,16 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
       dq[1] = min(dq[1], ((uint64_t)f32_order(__fsub_rn(Y, X)) << 32) | (uint32_t)i);
       dq[2] = min(dq[2], ((uint64_t)f32_order(-__fadd_rn(X, Y)) << 32) | (uint32_t)i);
       dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | (uint32_t)i);
+      // Table r takes only points that may lie strictly outside edge r (not
+      // certainly inside by the edge's FP32 filter): a point that strictly
+      // beats a region-r point in region r's sort and compared coordinates
+      // lies strictly outside edge r itself, so no other entry can ever
+      // discard anything.
 #pragma unroll
       for (int r = 0; r < 4; r++) {
-        float su = sort_u(X, Y, r);
-        if (su >= lo[r] && su <= hi[r])
+        const float su = sort_u(X, Y, r);
+        const float d = __fmaf_rn(fa[r], Y, __fmaf_rn(fb[r], X, fc[r]));
+        if (!(d > fe[r]) && su >= lo[r] && su <= hi[r])
           atomicMin(&tb[r][stair_pad(stair_bucket(su, lo[r], sc[r]))], cmp_view_order(X, Y, r));
       }
     }
