@@ -204,45 +204,68 @@ __device__ __forceinline__ bool grid_sync(const Ws& w, uint32_t& gen) {
 
 // Histogram phase: every sort tile, strided over the grid.
 __device__ void big_hist(const Job& j, const Ws& w, uint32_t total) {
+  // A CTA adds up the histograms of all its tiles of a set in shared memory
+  // and flushes them into the set's global histogram once (the global atomics
+  // would otherwise queue on the same 2304 words from every tile).
   __shared__ uint32_t h[kSortPasses][256];
   const int lane = threadIdx.x & 31;
   const int npass_key = j.dtype != DT_I32 ? 8 : 4;   // int32 keys have 4 zero bytes
+  constexpr int kItems = kSortTile / kThreads;
+  for (int q = threadIdx.x; q < kSortPasses * 256; q += kThreads) (&h[0][0])[q] = 0;
+  __syncthreads();
+  int cur = -1;            // set whose counts h holds (uniform across the CTA)
+  bool cur_first = false;  // whether this CTA took that set's first tile
+  auto flush = [&]() {
+    uint32_t* gh = w.hist + (size_t)cur * kSortPasses * 256;
+    const uint32_t n1 = w.ctl[cur].s1;
+    for (int q = threadIdx.x; q < kSortPasses * 256; q += kThreads) {
+      const uint32_t v = (&h[0][0])[q];
+      const int p = q >> 8;
+      if (p >= npass_key && p < 8) {
+        // constant zero byte: the set's first tile records all records in bin 0
+        if (cur_first && (q & 255) == 0) atomicAdd(gh + q, n1);
+      } else if (v) {
+        atomicAdd(gh + q, v);
+      }
+      (&h[0][0])[q] = 0;
+    }
+    __syncthreads();
+  };
   for (uint32_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
     const int s = seg_of(w.sort_start, j.nsets, tile);
+    if (s != cur) {
+      if (cur >= 0) flush();
+      cur = s;
+      cur_first = false;
+    }
     const SetDesc sd = get_set(j, s);
     const uint32_t lt = tile - w.sort_start[s];
+    if (lt == 0) cur_first = true;
     const uint32_t n1 = w.ctl[s].s1;
-    for (int q = threadIdx.x; q < kSortPasses * 256; q += kThreads) (&h[0][0])[q] = 0;
-    __syncthreads();
     const uint32_t b0 = lt * kSortTile;
     const uint32_t b1 = min(n1, b0 + kSortTile);
-    for (uint32_t i0 = b0; i0 < b1; i0 += kThreads) {
-      uint32_t i = i0 + threadIdx.x;
-      bool ok = i < b1;
-      uint64_t key = ok ? w.keyA[sd.off + i] : 0;
-      uint32_t val = ok ? w.valA[sd.off + i] : 0;
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; k++) {      // the thread's records, loads in flight together
+      const uint32_t i = b0 + k * kThreads + threadIdx.x;
+      key[k] = i < b1 ? w.keyA[sd.off + i] : 0ull;
+      val[k] = i < b1 ? w.valA[sd.off + i] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kItems; k++) {
+      const bool ok = b0 + k * kThreads + threadIdx.x < b1;
       const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok);
       for (int p = 0; p < kSortPasses; p++) {
         if (p >= npass_key && p < 8) continue;
-        uint32_t d = ok ? digit_of(key, val, p) : 0xFFFFFFFFu;
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t d = ok ? digit_of(key[k], val[k], p) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
         if (ok && lane == __ffs(peers & act) - 1) atomicAdd(&h[p][d], __popc(peers));
       }
     }
     __syncthreads();
-    uint32_t* gh = w.hist + (size_t)s * kSortPasses * 256;
-    for (int q = threadIdx.x; q < kSortPasses * 256; q += kThreads) {
-      uint32_t v = (&h[0][0])[q];
-      int p = q >> 8;
-      if (p >= npass_key && p < 8) {
-        // constant zero byte: the first tile of the set records all records in bin 0
-        if (lt == 0 && (q & 255) == 0) atomicAdd(gh + q, n1);
-      } else if (v) {
-        atomicAdd(gh + q, v);
-      }
-    }
-    __syncthreads();
   }
+  if (cur >= 0) flush();
 }
 
 // One radix pass: tiles taken in order from the pass's counter.
@@ -251,13 +274,16 @@ __device__ void big_pass(const Job& j, const Ws& w, int p, uint32_t total) {
   __shared__ uint32_t doff[256];
   __shared__ uint32_t gpre[256];
   __shared__ uint32_t wsum[kWarps];
-  __shared__ uint32_t sh_tile;
+  __shared__ uint32_t sh_tile, sh_full;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const uint32_t tag = (j.epoch << 4) | (uint32_t)p;
 
   for (;;) {
-    if (threadIdx.x == 0) sh_tile = atomicAdd(w.ctr + CT_SORT_TILE0 + p, 1u);
+    if (threadIdx.x == 0) {
+      sh_tile = atomicAdd(w.ctr + CT_SORT_TILE0 + p, 1u);
+      sh_full = 0;
+    }
     __syncthreads();
     const uint32_t tile = sh_tile;
     if (tile >= total) break;
@@ -268,14 +294,20 @@ __device__ void big_pass(const Job& j, const Ws& w, int p, uint32_t total) {
     const uint32_t n1 = w.ctl[s].s1;
     const uint32_t* gh = w.hist + (size_t)s * kSortPasses * 256;
 
-    // which earlier passes moved data (buffer parity), and whether this one does
-    int par = 0;
-    bool skip = false;
-    for (int q = 0; q <= p; q++) {
-      bool full = __syncthreads_or(gh[q * 256 + threadIdx.x] == n1) != 0;
-      if (q < p) par ^= full ? 0 : 1;
-      else skip = full;
+    // which earlier passes moved data (buffer parity), and whether this one
+    // does: a pass whose digit histogram has all records in one bin moves
+    // nothing.  Every thread reads its bin of passes 0..p at once, the CTA
+    // ORs the bit masks.
+    {
+      uint32_t fm = 0;
+      for (int q = 0; q <= p; q++) fm |= (gh[q * 256 + threadIdx.x] == n1 ? 1u : 0u) << q;
+      fm = __reduce_or_sync(0xFFFFFFFFu, fm);
+      if (lane == 0 && fm) atomicOr(&sh_full, fm);
     }
+    __syncthreads();
+    const uint32_t full = sh_full;
+    const int par = __popc(~full & ((1u << p) - 1u)) & 1;
+    const bool skip = (full >> p) & 1u;
     if (skip) continue;   // uniform across the CTA
     if (lt == 0 && threadIdx.x == 0) w.ctl[s].passes++;   // one CTA per (pass, set); passes are barrier-separated
     const uint64_t* kin = par ? w.keyB : w.keyA;
