@@ -394,3 +394,23 @@ def test_repeated_calls_and_streams_are_independent():
     for (ia, ca), (ib, cb) in outs:
         assert np.array_equal(ia[:int(ca.item())].cpu().numpy(), wa)
         assert np.array_equal(ib[:int(cb.item())].cpu().numpy(), wb)
+
+
+# ------------------------------- shared-memory sort, cluster form, crowded
+
+def test_cluster_sort_crowded_region():
+    """One region of about 10k round-1 survivors in columns of 40 equal
+    sort coordinates: the region is split over the cluster and the leader
+    sorts with the radix path (crowded buckets).  The lower-left arc is the
+    quarter circle of radius 1 around (1, 1); column k holds the arc point
+    and 39 points just above it."""
+    xs = np.arange(1, 256) / 256.0
+    g = 1.0 - np.sqrt(1.0 - (xs - 1.0) ** 2)
+    pts = [np.array([[0.0, 1.0], [1.0, 0.0], [2.0, 1.0], [1.0, 2.0]])]
+    for jj in range(40):
+        pts.append(np.stack([xs, g + jj * 1e-7], axis=1))
+    p = np.concatenate(pts)
+    p = p[np.random.default_rng(12).permutation(len(p))]
+    st = cch.stages(torch.from_numpy(p).to(DEV))
+    assert int(st["counts"][1]) >= 4096, st["counts"][:5]
+    check(p)
