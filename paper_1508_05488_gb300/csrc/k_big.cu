@@ -205,10 +205,11 @@ __device__ __forceinline__ bool grid_sync(const Ws& w, uint32_t& gen) {
 // Histogram phase: every sort tile, strided over the grid.
 __device__ void big_hist(const Job& j, const Ws& w, uint32_t total) {
   // A CTA adds up the histograms of all its tiles of a set in shared memory
-  // and flushes them into the set's global histogram once (the global atomics
-  // would otherwise queue on the same 2304 words from every tile).
+  // (one shared atomic per record and digit: cheaper here than ranking equal
+  // digits with match.any) and flushes them into the set's global histogram
+  // once (the global atomics would otherwise queue on the same 2304 words
+  // from every tile).
   __shared__ uint32_t h[kSortPasses][256];
-  const int lane = threadIdx.x & 31;
   const int npass_key = j.dtype != DT_I32 ? 8 : 4;   // int32 keys have 4 zero bytes
   constexpr int kItems = kSortTile / kThreads;
   for (int q = threadIdx.x; q < kSortPasses * 256; q += kThreads) (&h[0][0])[q] = 0;
@@ -255,12 +256,9 @@ __device__ void big_hist(const Job& j, const Ws& w, uint32_t total) {
 #pragma unroll
     for (int k = 0; k < kItems; k++) {
       const bool ok = b0 + k * kThreads + threadIdx.x < b1;
-      const uint32_t act = __ballot_sync(0xFFFFFFFFu, ok);
       for (int p = 0; p < kSortPasses; p++) {
         if (p >= npass_key && p < 8) continue;
-        const uint32_t d = ok ? digit_of(key[k], val[k], p) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        if (ok && lane == __ffs(peers & act) - 1) atomicAdd(&h[p][d], __popc(peers));
+        if (ok) atomicAdd(&h[p][digit_of(key[k], val[k], p)], 1u);
       }
     }
     __syncthreads();
