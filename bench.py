@@ -717,6 +717,13 @@ def main():
         step()
     stage_all, calls_all = cch.profile_read()
     stage_all = {k: v / max(calls_all, 1) for k, v in stage_all.items()}
+    # the same per set, for the streaming kernels' fraction on each
+    stage_set = {}
+    for k in kinds:
+        for _ in range(3):
+            cch.hull_async(dpts[k], outs[k][0], outs[k][1], stream=stream)
+        ms_k, calls_k = cch.profile_read()
+        stage_set[k] = {s_: v / max(calls_k, 1) for s_, v in ms_k.items()}
     # ... and, inside the timed region, events around the dominant streaming
     # kernel only
     dom = max(("k_extremes", "k_classify"), key=lambda k: stage_all[k])
@@ -762,6 +769,12 @@ def main():
     # the whole step against the method's floor: two reads of every input
     # point (the extremes must be known before the classification)
     step_bytes = 2 * 16.0 * args.n * len(kinds)
+    # per set, from the profiled pass (events around every stage): the two
+    # streaming kernels' 16 B per point over their stage time
+    roofline["per_set"] = {
+        k: {kern: {"ms": v[kern], "frac": alg_bytes / (v[kern] * 1e-3) / 1e9 / hbm}
+            for kern in ("k_extremes", "k_classify") if v.get(kern)}
+        for k, v in stage_set.items()}
     roofline["step"] = {"algorithmic_bytes": step_bytes, "ms": ms_step,
                         "achieved": step_bytes / (ms_step * 1e-3) / 1e9,
                         "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm}
