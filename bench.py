@@ -299,7 +299,8 @@ def serve_bench(cch, torch, dev, requests_per_load, window=256):
     distinct requests, drawn in device memory and submitted from there
     (cch_serve_submit_device: the request state stays device-resident).
     First the saturated rate (closed loop, at most `window` requests
-    outstanding), then offered loads of 0.5, 0.8 and 0.95 of it.  Every
+    outstanding, measured twice: the higher is reported with the lower
+    beside it), then offered loads of 0.5, 0.8 and 0.95 of the lower.  Every
     result is compared with the hull of the same request computed alone
     (cch_hull).  `hulls_per_s` counts every request over first submit ->
     last result; `drain_ms` is last result - last arrival."""
@@ -344,8 +345,13 @@ def serve_bench(cch, torch, dev, requests_per_load, window=256):
                 "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "samples": len(res),
                 "identical_to_alone": bool(ok)}
 
-    sat = run(None)
-    loads = [run(f * sat["hulls_per_s"]) for f in (0.5, 0.8, 0.95)]
+    # the saturated rate twice (it varies from run to run on a shared box);
+    # the offered loads are fractions of the lower one
+    sat, sat2 = run(None), run(None)
+    if sat2["hulls_per_s"] > sat["hulls_per_s"]:
+        sat, sat2 = sat2, sat
+    sat["other_run_hulls_per_s"] = sat2["hulls_per_s"]
+    loads = [run(f * sat2["hulls_per_s"]) for f in (0.5, 0.8, 0.95)]
     sizes = [int(r.shape[0]) for r in reqs]
     del reqs
     torch.cuda.empty_cache()
