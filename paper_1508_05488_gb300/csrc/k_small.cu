@@ -337,28 +337,27 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(Job j, Ws w) {
       }
     }
     if (split) {
-      // merge the cluster's tables: this CTA takes words [w0, w1) of the
-      // (contiguous) two tables, minimum over the eight copies, written back
-      // to every copy (two words a step, their remote loads in flight together)
+      // merge the cluster's tables: this CTA takes 16-byte groups [q0, q1)
+      // of the (contiguous) two tables, minimum over the eight copies,
+      // written back to every copy
       cg::cluster_group cl = cg::this_cluster();
       cl.sync();
-      constexpr uint32_t W = kPadA + kPadB, S = (W + CL - 1) / CL;
-      const uint32_t w0 = rank * S, w1 = min(W, w0 + S);
-      for (uint32_t x = w0 + tid; x < w1; x += 2 * kSmThreads) {
-        const uint32_t x2 = x + kSmThreads;
-        uint32_t v[CL], v2[CL];
+      static_assert((kPadA + kPadB) % 4 == 0, "the tables are whole 16-byte groups");
+      constexpr uint32_t W4 = (kPadA + kPadB) / 4, S4 = (W4 + CL - 1) / CL;
+      const uint32_t q0 = rank * S4, q1 = min(W4, q0 + S4);
+      uint4* t4 = reinterpret_cast<uint4*>(vminA);
+      for (uint32_t x = q0 + tid; x < q1; x += kSmThreads) {
+        uint4 v[CL];
 #pragma unroll
-        for (int c = 0; c < CL; c++) {
-          v[c] = cl.map_shared_rank(vminA, c)[x];
-          v2[c] = x2 < w1 ? cl.map_shared_rank(vminA, c)[x2] : 0xFFFFFFFFu;
+        for (int c = 0; c < CL; c++) v[c] = cl.map_shared_rank(t4, c)[x];
+        uint4 mn = v[0];
+#pragma unroll
+        for (int c = 1; c < CL; c++) {
+          mn.x = min(mn.x, v[c].x); mn.y = min(mn.y, v[c].y);
+          mn.z = min(mn.z, v[c].z); mn.w = min(mn.w, v[c].w);
         }
 #pragma unroll
-        for (int c = 1; c < CL; c++) { v[0] = min(v[0], v[c]); v2[0] = min(v2[0], v2[c]); }
-#pragma unroll
-        for (int c = 0; c < CL; c++) {
-          cl.map_shared_rank(vminA, c)[x] = v[0];
-          if (x2 < w1) cl.map_shared_rank(vminA, c)[x2] = v2[0];
-        }
+        for (int c = 0; c < CL; c++) cl.map_shared_rank(t4, c)[x] = mn;
       }
       cl.sync();
     } else {
