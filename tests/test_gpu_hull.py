@@ -231,6 +231,20 @@ def test_batched_matches_per_set():
     del rng
 
 
+def test_batched_few_large_sets_cluster_split():
+    """A batched call of three sets (the cluster form of the per-region
+    sort): the 5M disk's regions hold about 6k round-1 survivors each and are
+    split over their clusters; the other two sets' regions are not."""
+    parts = [inputs.disk_f64(5_000_000, 31), inputs.square_f64(20_000, 32), inputs.gauss_f64(3_000_000, 33)]
+    p = np.concatenate(parts)
+    off = np.concatenate([[0], np.cumsum([len(q) for q in parts])]).astype(np.int64)
+    st = cch.stages(torch.from_numpy(parts[0]).to(DEV))
+    assert int(st["counts"][1:5].max()) >= 4096, st["counts"][:5]
+    res = cch.hull_batched(torch.from_numpy(p).to(DEV), off)
+    for s in range(3):
+        assert np.array_equal(res[s].cpu().numpy(), oracle.hull(parts[s])), s
+
+
 def test_batched_int32_many_sets():
     p, off = inputs.batched_i32(300, seed=3, lo=16, hi=20_000)
     res = cch.hull_batched(torch.from_numpy(p).to(DEV), off)
