@@ -10,8 +10,9 @@
 //                       (steps 2-3)
 //       k_gather        survivors moved into region-major order; per set the
 //                       choice between the two sort paths
-//   a3+ k_small         per (set, region) in one CTA: Table 1 sort and Fig. 2
-//   a4                  SPA in shared memory (steps 4-5)
+//   a3+ k_small         per (set, region) in one CTA (or, for calls of a few
+//   a4                  sets, an 8-CTA cluster): Table 1 sort and Fig. 2 SPA
+//                       in shared memory (steps 4-5)
 //       k_big           sets with a region above kSmallMax records: LSD radix
 //                       sort and SPA as a segmented prefix-minimum scan, one
 //                       cooperative persistent kernel (steps 4-5)
