@@ -128,6 +128,16 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
+def hull_alg_bytes(S, n, s1, s2, h, W=None):
+    """The method's algorithmic bytes for one hull (the measurement
+    contract's accounting): the input read twice (extremes, then
+    classification), the round-1 records written, sorted (one read and one
+    write), scanned, the SPA survivors written and read by the chain step,
+    and the hull written.  S = bytes per input point, W = record bytes."""
+    W = W or (20 if S == 16 else 12)
+    return 2 * S * n + W * s1 + 2 * W * s1 + (W * s1 + W * s2) + W * s2 + 4 * h
+
+
 def whole_job_rate(points_all_ranks, ms_step):
     """Mpoints/s of the whole job: every rank's points over the slowest rank's step time."""
     return points_all_ranks / (ms_step * 1e-3) / 1e6
@@ -416,7 +426,9 @@ def extra_configs_bench(cch, torch, dev, reps, hbm):
         rec = 12                     # record: 8-byte sort key + 4-byte value
         big_bytes = rec * s1 + passes * 2 * rec * s1 + (4 + S) * s1 + (S + 4) * s2 if passes else 0
         big_ms = st_ms.get("big", 0.0)
+        b_alg = hull_alg_bytes(S, n, s1, s2, h)
         entry = {"config": desc, "n": n, "dtype": dt, "ms_per_hull": ms, "mpoints_s": n / ms / 1e3,
+                 "hull_roofline": {"algorithmic_bytes": b_alg, "frac": b_alg / (ms * 1e-3) / 1e9 / hbm},
                  "hull_size": h, "stage_ms_per_hull": st_ms,
                  "round1_paper": int(paper["counts"][0]), "round1": s1, "spa": s2,
                  "identical_spa_both_modes": all(bool((a == b).all()) and len(a) == len(b)
@@ -528,8 +540,7 @@ def survivors(kinds, sizes, reps):
             s1p = int(sum(len(a) for a in ours["r1"]))
             s2 = int(sum(len(a) for a in paper["spa"]))
             h = int(paper["count"])
-            S, W = 16, 20
-            balg = 2 * S * n + W * s1 + 2 * W * s1 + (W * s1 + W * s2) + W * s2 + 4 * h
+            balg = hull_alg_bytes(16, n, s1, s2, h)
             rows.append({"kind": kind, "n": n, "round1": s1, "round1_prefiltered": s1p, "spa": s2, "hull": h,
                          "us_per_hull": round(us, 1), "mpoints_s": round(n / us, 1),
                          "alg_bytes": balg, "alg_gbs": round(balg / us / 1e3, 1)})
@@ -784,6 +795,22 @@ def main():
     roofline["step"] = {"algorithmic_bytes": step_bytes, "ms": ms_step,
                         "achieved": step_bytes / (ms_step * 1e-3) / 1e9,
                         "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm}
+
+    # each set's whole hull against its algorithmic bytes (measured s1, s2, h)
+    for k in kinds:
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(10):
+            cch.hull_async(dpts[k], outs[k][0], outs[k][1], stream=stream)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        ms_k = h0.elapsed_time(h1) / 10
+        st_k = cch.stages(dpts[k])
+        s1, s2 = int(st_k["counts"][0]), int(st_k["counts"][5:9].sum())
+        b_k = hull_alg_bytes(16, args.n, s1, s2, int(st_k["count"]))
+        roofline["per_set"][k]["hull"] = {"ms": ms_k, "round1": s1, "spa": s2, "algorithmic_bytes": b_k,
+                                          "frac": b_k / (ms_k * 1e-3) / 1e9 / hbm}
 
     # the same step with the three independent hulls issued on three streams
     # (each a single-hull call with its own workspace): one hull's
