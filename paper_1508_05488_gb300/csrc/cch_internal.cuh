@@ -61,7 +61,8 @@ constexpr int kClsMinTile = kClsTileF64 < kClsTileI32 ? kClsTileF64 : kClsTileI3
 // sample of the set.
 constexpr int kStairB = 1024;          // buckets per region
 constexpr int64_t kStairSample = int64_t(1) << 20;   // sample points per set (the last ones)
-constexpr int kStairChunk = 4096;      // sample points per CTA
+constexpr int kStairChunk = 2048;      // sample points per k_stairs CTA (eight per thread)
+constexpr int kStairLB = 512;          // buckets per region of a k_stairs CTA's own table
 constexpr int64_t kStairMin = 8192;    // smallest sample of a set
 constexpr int kPlanTiles = 64;         // a2 tiles per survivor-count chunk
 constexpr int kGatherSplit = 8;        // gather CTAs per chunk (all of them move a dense chunk)
@@ -914,6 +915,10 @@ __device__ __forceinline__ void move_subslots(const Job& j, const Ws& w, const S
 // griddepcontrol.launch_dependents, measured slower: their CTAs queue for
 // resources the running kernel holds.)
 __device__ __forceinline__ void griddep_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// The one exception: a1 lets k_stairs be scheduled once its tile loops are
+// done (griddep_release), and k_stairs reduces its sample -- input points
+// only -- before its griddep_enter, while a1's last CTA sets the set up.
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -834,6 +834,10 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     }
   }
 
+  // the tile loops are done: k_stairs may be scheduled (it reads none of a1's
+  // results before its griddep_enter)
+  griddep_release();
+
   // reduction over the consumer warps
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -948,10 +952,6 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
 
 // ------------------------------------------------------------ stairs
 
-// Padded index of a stairs table word (one spare word in 32): 64 threads
-// reading 16 consecutive words each hit 32 different banks.
-__device__ __forceinline__ int stair_pad(int b) { return b + (b >> 5); }
-
 // Exclusive minimum of `v` over the lower threads of the same 64-thread
 // region group (threads 64r .. 64r+63, two warps); sw holds one word per
 // warp.  Ends with the CTA synchronised.
@@ -972,13 +972,45 @@ __device__ __forceinline__ uint32_t region_excl_min(uint32_t v, uint32_t* sw) {
   return ex;
 }
 
+// The float whose order word (f32_order) is k.
+__device__ __forceinline__ float f32_unorder(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+}
+
+// Bucket of u under the map (lo, scale) of NB buckets: non-decreasing in u.
+template <int NB>
+__device__ __forceinline__ int bucket_of(float u, float lo, float scale) {
+  const int b = __float2int_rd(__fmul_rn(__fsub_rn(u, lo), scale));
+  return min(max(b, 0), NB - 1);
+}
+
+// k_stairs: the dominance table of every set from the sample.  Each CTA
+// takes kStairChunk sample points (eight per thread, loaded once and held in
+// registers).  Before its griddep_enter it reads only
+// input points, so it runs during a1's tail (a1 releases it after its tile
+// loops): pass 1 finds the chunk's extent and the quadrant extremes of the
+// dominance box, pass 2 keeps, per region r and bucket of the chunk's own map
+// (kStairLB buckets over the extent of the region's sort coordinate u =
+// sort_u), the smallest (compared word v = cmp_view_order) << 32 | (order
+// word of u), and the buckets whose v is below every lower bucket's are the
+// chunk's staircase steps: sample points with their exact views.  After a1
+// (regions, their maps E_r -> E_{r+1}, the cleared table) each step goes
+// into the set's table at its bucket of the region's map; the last CTA of
+// the set turns the bucket minima into exclusive prefix minima.  A step Q in
+// a lower bucket than a region-r point P and with a smaller v beats P
+// strictly in both coordinates, so P is no SPA survivor; every step is a
+// sample point, so which steps reach the table only changes how much the
+// prefilter drops.
 template <int DT>
-__global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
-  griddep_enter();
-  constexpr int kTb = kStairB + kStairB / 32;   // padded table (one spare word in 32)
-  static_assert(kThreads == 4 * 64 && kStairB == 64 * 16, "64 threads x 16 buckets per region");
-  __shared__ uint32_t tb[4][kTb];
+__global__ void __launch_bounds__(kThreads, 4) k_stairs(Job j, Ws w) {
+  static_assert(kThreads == 4 * 64 && kStairB == 64 * 16 && kStairLB == 64 * 8, "64 threads per region");
+  static_assert(kStairChunk % kThreads == 0, "whole points per thread");
+  __shared__ uint64_t lt[4][kStairLB];
   __shared__ uint32_t sw[kWarps];
+  __shared__ float sred[kWarps][4];
+  __shared__ uint64_t sdq[kWarps][4];
+  __shared__ int sidx[4];
+  __shared__ float sqx[4], sqy[4];
   __shared__ int last;
   const int chunk = blockIdx.x;
   int s = 0;
@@ -990,79 +1022,150 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
     }
     s = lo;
   }
-  const SetDesc sd = get_set(j, s);
-  const SetCtl& c = w.ctl[s];
-  if (c.status != 0 || !(c.flags & SF_STAIRS)) return;   // uniform; table unused
-  float lo[4], hi[4], sc[4], fa[4], fb[4], fc[4], fe[4];
-#pragma unroll
-  for (int r = 0; r < 4; r++) {
-    lo[r] = c.slo[r]; hi[r] = c.shi[r]; sc[r] = c.sscale[r];
-    fa[r] = c.fA[r]; fb[r] = -c.fB[r]; fc[r] = c.fC[r]; fe[r] = c.fE[r];
+  if (j.opts & OPT_NO_PREFILTER) {   // uniform; the table is unused
+    griddep_enter();   // every CTA exits after a1 has completed: a2 waits for k_stairs only
+    return;
   }
-  for (int i = threadIdx.x; i < 4 * kTb; i += kThreads) (&tb[0][0])[i] = 0xFFFFFFFFu;
-  __syncthreads();
+  const SetDesc sd = get_set(j, s);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 4 * kStairLB; i += kThreads) (&lt[0][0])[i] = ~0ull;
 
   const int64_t m = stairs_sample(sd.n, j.tune);
   const int64_t c0 = sd.n - m + (int64_t)(chunk - sd.chunk3) * kStairChunk;
   const int64_t c1 = min(sd.n, c0 + kStairChunk);
+  // the chunk's points, U per thread, held in registers for both passes
+  constexpr int U = kStairChunk / kThreads;
+  float vx[U], vy[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int64_t i = c0 + u * kThreads + tid;
+    if (i < c1) view_at<DT>(j, sd.off + i, vx[u], vy[u]);
+  }
+  // pass 1: the chunk's extent and the quadrant extremes
+  const float inf = __int_as_float(0x7F800000);
+  float ext[4] = {inf, -inf, inf, -inf};           // min x, max x, min y, max y
   uint64_t dq[4] = {~0ull, ~0ull, ~0ull, ~0ull};   // best score key << 32 | index per quadrant
-  constexpr int U = 8;
-  for (int64_t b0 = c0; b0 < c1; b0 += (int64_t)kThreads * U) {
-    float vx[U], vy[U];
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      int64_t i = b0 + u * kThreads + threadIdx.x;
-      if (i < c1) view_at<DT>(j, sd.off + i, vx[u], vy[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      int64_t i = b0 + u * kThreads + threadIdx.x;
-      if (i >= c1) continue;
-      const float X = vx[u], Y = vy[u];
-      // quadrant scores: lower-left x+y, lower-right y-x, upper-right -x-y,
-      // upper-left x-y (smaller is further into the quadrant)
-      dq[0] = min(dq[0], ((uint64_t)f32_order(__fadd_rn(X, Y)) << 32) | (uint32_t)i);
-      dq[1] = min(dq[1], ((uint64_t)f32_order(__fsub_rn(Y, X)) << 32) | (uint32_t)i);
-      dq[2] = min(dq[2], ((uint64_t)f32_order(-__fadd_rn(X, Y)) << 32) | (uint32_t)i);
-      dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | (uint32_t)i);
-      // Table r takes only points that may lie strictly outside edge r (not
-      // certainly inside by the edge's FP32 filter): a point that strictly
-      // beats a region-r point in region r's sort and compared coordinates
-      // lies strictly outside edge r itself, so no other entry can ever
-      // discard anything.
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const float su = sort_u(X, Y, r);
-        const float d = __fmaf_rn(fa[r], Y, __fmaf_rn(fb[r], X, fc[r]));
-        if (!(d > fe[r]) && su >= lo[r] && su <= hi[r])
-          atomicMin(&tb[r][stair_pad(stair_bucket(su, lo[r], sc[r]))], cmp_view_order(X, Y, r));
-      }
-    }
+  for (int u = 0; u < U; u++) {
+    const int64_t i = c0 + u * kThreads + tid;
+    if (i >= c1) continue;
+    const float X = vx[u], Y = vy[u];
+    ext[0] = fminf(ext[0], X); ext[1] = fmaxf(ext[1], X);
+    ext[2] = fminf(ext[2], Y); ext[3] = fmaxf(ext[3], Y);
+    // quadrant scores: lower-left x+y, lower-right y-x, upper-right -x-y,
+    // upper-left x-y (smaller is further into the quadrant)
+    dq[0] = min(dq[0], ((uint64_t)f32_order(__fadd_rn(X, Y)) << 32) | (uint32_t)i);
+    dq[1] = min(dq[1], ((uint64_t)f32_order(__fsub_rn(Y, X)) << 32) | (uint32_t)i);
+    dq[2] = min(dq[2], ((uint64_t)f32_order(-__fadd_rn(X, Y)) << 32) | (uint32_t)i);
+    dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | (uint32_t)i);
   }
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ext[0] = fminf(ext[0], __shfl_xor_sync(0xFFFFFFFFu, ext[0], o));
+    ext[1] = fmaxf(ext[1], __shfl_xor_sync(0xFFFFFFFFu, ext[1], o));
+    ext[2] = fminf(ext[2], __shfl_xor_sync(0xFFFFFFFFu, ext[2], o));
+    ext[3] = fmaxf(ext[3], __shfl_xor_sync(0xFFFFFFFFu, ext[3], o));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dq[q] = min(dq[q], __shfl_xor_sync(0xFFFFFFFFu, dq[q], o));
-    if ((threadIdx.x & 31) == 0 && dq[q] != ~0ull)
-      atomicMax((unsigned long long*)&w.ctl[s].dq[q], (unsigned long long)~dq[q]);
+    for (int q = 0; q < 4; q++) dq[q] = min(dq[q], __shfl_xor_sync(0xFFFFFFFFu, dq[q], o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) { sred[warp][k] = ext[k]; sdq[warp][k] = dq[k]; }
   }
   __syncthreads();
-  // Merge into the set's tables.  The tables only ever feed exclusive prefix
-  // minima over lower buckets, so an entry that is not below this CTA's own
-  // minimum over the lower buckets changes nothing (the lower bucket already
-  // holds a value at least as small): only the CTA's staircase steps go out.
-  // 64 threads per region, 16 consecutive buckets each.
-  uint32_t* g = w.stairs + (size_t)s * 4 * kStairB;
-  const int rr = threadIdx.x >> 6, ru = threadIdx.x & 63;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    float v = sred[0][k];
+#pragma unroll
+    for (int q = 1; q < kWarps; q++) v = (k & 1) ? fmaxf(v, sred[q][k]) : fminf(v, sred[q][k]);
+    ext[k] = v;
+  }
+  // one atomic per quadrant and CTA (the set's words take one from every
+  // CTA); the control words were cleared before a1, which leaves dq alone
+  if (tid < 4) {
+    uint64_t d = sdq[0][tid];
+#pragma unroll
+    for (int q = 1; q < kWarps; q++) d = min(d, sdq[q][tid]);
+    if (d != ~0ull) atomicMax((unsigned long long*)&w.ctl[s].dq[tid], (unsigned long long)~d);
+    sidx[tid] = d == ~0ull ? -1 : (int)((int64_t)(uint32_t)d - c0);   // the chunk's quadrant extreme
+  }
+  __syncthreads();
+  // its owner publishes its view: a point that the chunk's quadrant extreme
+  // of region r beats strictly in both coordinates is no step of region r
+  // (R1 lower-left, R2 lower-right, R3 upper-right, R4 upper-left)
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int k = sidx[q];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (k == u * kThreads + tid) { sqx[q] = vx[u]; sqy[q] = vy[u]; }
+    if (k < 0 && tid == 0) { sqx[q] = __int_as_float(0x7FC00000); sqy[q] = sqx[q]; }   // NaN: beats nothing
+  }
+  // the chunk's map of region r: u over [a, b] (R1 x, R2 y, R3 -x, R4 -y);
+  // an empty or unbounded extent puts everything into bucket 0
+  float lo1[4], sc1[4];
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const int e = (r & 1) ? 2 : 0;
+    const float a = r < 2 ? ext[e] : -ext[e + 1], b = r < 2 ? ext[e + 1] : -ext[e];
+    const float wd = __fsub_rn(b, a);
+    lo1[r] = a;
+    sc1[r] = (wd > 0.f && wd < inf) ? __fdiv_rn((float)kStairLB, wd) : 0.f;
+  }
+  __syncthreads();
+  // pass 2: the smallest (v, u) per bucket (the shared word is read first:
+  // most points change nothing)
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    if (c0 + u * kThreads + tid >= c1) continue;
+    const float X = vx[u], Y = vy[u];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const float qx = sqx[r], qy = sqy[r];
+      const bool bx = (r == 0 || r == 3) ? (qx < X) : (qx > X);
+      const bool by = r < 2 ? (qy < Y) : (qy > Y);
+      if (bx && by) continue;
+      const float su = sort_u(X, Y, r);
+      const uint64_t e = ((uint64_t)cmp_view_order(X, Y, r) << 32) | f32_order(su);
+      unsigned long long* slot = (unsigned long long*)&lt[r][bucket_of<kStairLB>(su, lo1[r], sc1[r])];
+      if (e < *slot) atomicMin(slot, (unsigned long long)e);
+    }
+  }
+  __syncthreads();
+  // the chunk's steps: 64 threads per region, 8 buckets each
+  const int rr = tid >> 6, ru = tid & 63;
+  constexpr int Q = kStairLB / 64;
+  uint64_t loc[Q];
+  uint32_t stepm = 0;
   {
-    uint32_t loc[16];
     uint32_t mn = 0xFFFFFFFFu;
 #pragma unroll
-    for (int q = 0; q < 16; q++) { loc[q] = tb[rr][stair_pad(ru * 16 + q)]; mn = min(mn, loc[q]); }
+    for (int q = 0; q < Q; q++) { loc[q] = lt[rr][ru * Q + q]; mn = min(mn, (uint32_t)(loc[q] >> 32)); }
     uint32_t ex = region_excl_min(mn, sw);
 #pragma unroll
-    for (int q = 0; q < 16; q++)
-      if (loc[q] < ex) { atomicMin(g + rr * kStairB + ru * 16 + q, loc[q]); ex = loc[q]; }
+    for (int q = 0; q < Q; q++) {
+      const uint32_t v = (uint32_t)(loc[q] >> 32);
+      if (v < ex) { stepm |= 1u << q; ex = v; }
+    }
+  }
+
+  griddep_enter();   // a1 has completed: the set's regions, maps and a cleared table
+  const SetCtl& c = w.ctl[s];
+  if (c.status != 0 || !(c.flags & SF_STAIRS)) return;   // uniform; table unused
+  uint32_t* g = w.stairs + (size_t)s * 4 * kStairB;
+  {
+    // the table word is read first: most CTAs' steps are beaten by others'
+    const float lo = c.slo[rr], sc = c.sscale[rr];
+    int bk[Q];
+    uint32_t cur[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      bk[q] = rr * kStairB + stair_bucket(f32_unorder((uint32_t)loc[q]), lo, sc);
+      cur[q] = ((stepm >> q) & 1u) ? __ldcg(g + bk[q]) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++)
+      if ((uint32_t)(loc[q] >> 32) < cur[q]) atomicMin(g + bk[q], (uint32_t)(loc[q] >> 32));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1098,19 +1201,19 @@ __global__ void __launch_bounds__(kThreads) k_stairs(Job j, Ws w) {
   }
   // exclusive prefix minimum per region, seeded with the first extreme
   {
-    uint32_t loc[16];
+    uint32_t lv[16];
 #pragma unroll
-    for (int q = 0; q < 4; q++) { loc[4 * q] = tv[q].x; loc[4 * q + 1] = tv[q].y; loc[4 * q + 2] = tv[q].z; loc[4 * q + 3] = tv[q].w; }
+    for (int q = 0; q < 4; q++) { lv[4 * q] = tv[q].x; lv[4 * q + 1] = tv[q].y; lv[4 * q + 2] = tv[q].z; lv[4 * q + 3] = tv[q].w; }
     uint32_t mn = 0xFFFFFFFFu;
 #pragma unroll
-    for (int q = 0; q < 16; q++) mn = min(mn, loc[q]);
+    for (int q = 0; q < 16; q++) mn = min(mn, lv[q]);
     float EX, EY;
     view_at<DT>(j, sd.off + c.eidx[rr], EX, EY);
     uint32_t ex = min(region_excl_min(mn, sw), cmp_view_order(EX, EY, rr));
     uint4 o[4];
 #pragma unroll
     for (int q = 0; q < 16; q++) {
-      const uint32_t v = loc[q];
+      const uint32_t v = lv[q];
       (&o[q >> 2].x)[q & 3] = ex;
       ex = min(ex, v);
     }
