@@ -102,11 +102,29 @@ __device__ __forceinline__ bool lex_less(const Lex& a, const Lex& b) {
 __device__ __forceinline__ void lex_min_into(Lex& a, const Lex& b) {
   if (lex_less(b, a)) a = b;
 }
-__device__ __forceinline__ Lex lex_shfl(const Lex& v, int o) {
+// Warp-wide minima in every lane, one warp reduction (redux) per 32-bit
+// word: a 64-bit minimum takes its high word's minimum, then the low words'
+// minimum over the lanes that hold it; the lexicographic minimum of
+// (k1, k2, idx) goes word by word the same way.
+__device__ __forceinline__ uint64_t u64_warp_min(uint64_t v) {
+  const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(v >> 32));
+  const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(v >> 32) == hi ? (uint32_t)v : 0xFFFFFFFFu);
+  return kw(hi, lo);
+}
+__device__ __forceinline__ Lex lex_warp_min(const Lex& v) {
+  const uint32_t w0 = (uint32_t)(v.k1 >> 32), w1 = (uint32_t)v.k1, w2 = (uint32_t)(v.k2 >> 32), w3 = (uint32_t)v.k2;
+  const uint32_t m0 = __reduce_min_sync(0xFFFFFFFFu, w0);
+  bool t = w0 == m0;
+  const uint32_t m1 = __reduce_min_sync(0xFFFFFFFFu, t ? w1 : 0xFFFFFFFFu);
+  t = t && w1 == m1;
+  const uint32_t m2 = __reduce_min_sync(0xFFFFFFFFu, t ? w2 : 0xFFFFFFFFu);
+  t = t && w2 == m2;
+  const uint32_t m3 = __reduce_min_sync(0xFFFFFFFFu, t ? w3 : 0xFFFFFFFFu);
+  t = t && w3 == m3;
   Lex r;
-  r.k1 = __shfl_xor_sync(0xFFFFFFFFu, v.k1, o);
-  r.k2 = __shfl_xor_sync(0xFFFFFFFFu, v.k2, o);
-  r.idx = __shfl_xor_sync(0xFFFFFFFFu, v.idx, o);
+  r.k1 = kw(m0, m1);
+  r.k2 = kw(m2, m3);
+  r.idx = __reduce_min_sync(0xFFFFFFFFu, t ? v.idx : 0xFFFFFFFFu);
   return r;
 }
 
@@ -838,18 +856,29 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   // results before its griddep_enter)
   griddep_release();
 
-  // reduction over the consumer warps
+  // reduction over the consumer warps, then over the warps' results in warp 0
+  auto warp_reduce = [&]() {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
-    amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
-    lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
+    for (int k = 0; k < 4; k++) best[k] = lex_warp_min(best[k]);
+    amin = __reduce_min_sync(0xFFFFFFFFu, amin);
+    lomag = __reduce_min_sync(0xFFFFFFFFu, lomag);
     if constexpr (OCT) {
 #pragma unroll
-      for (int q = 0; q < 4; q++) dqm[q] = min(dqm[q], __shfl_xor_sync(0xFFFFFFFFu, dqm[q], o));
+      for (int q = 0; q < 4; q++) dqm[q] = u64_warp_min(dqm[q]);
     }
-  }
+  };
+  auto warp0_gather = [&]() {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (lane < kClsConsumers) best[k] = red[lane][k];
+      else { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
+    }
+    amin = lane < kClsConsumers ? red_amin[lane] : 0x7FFFFFFFu;
+    lomag = lane < kClsConsumers ? red_lomag[lane] : 0x7FFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < 4; q++) dqm[q] = lane < kClsConsumers ? red_dq[lane][q] : ~0ull;
+  };
+  warp_reduce();
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; k++) red[warp][k] = best[k];
@@ -859,13 +888,11 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     for (int q = 0; q < 4; q++) red_dq[warp][q] = dqm[q];
   }
   consumers_sync();
+  if (warp == 0) {
+    warp0_gather();
+    warp_reduce();
+  }
   if (tid == 0) {
-    for (int q = 1; q < kClsConsumers; q++) {
-      for (int k = 0; k < 4; k++) lex_min_into(best[k], red[q][k]);
-      amin = min(amin, red_amin[q]);
-      lomag = min(lomag, red_lomag[q]);
-      for (int k = 0; k < 4; k++) dqm[k] = min(dqm[k], red_dq[q][k]);
-    }
     Part& pt = w.part[chunk];
     for (int k = 0; k < 4; k++) { pt.k1[k] = best[k].k1; pt.k2[k] = best[k].k2; pt.idx[k] = best[k].idx; }
     pt.bad = amin;
@@ -886,8 +913,8 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   amin = 0x7FFFFFFFu;
   lomag = 0x7FFFFFFFu;
   for (int k = 0; k < 4; k++) dqm[k] = ~0ull;
-  for (int q = threadIdx.x; q < sd.nchunk1; q += kClsConsumers * 32) {
-    const Part& pt = w.part[sd.chunk1 + q];
+  auto fold = [&](const Part& pt) {
+#pragma unroll
     for (int k = 0; k < 4; k++) {
       Lex v{pt.k1[k], pt.k2[k], pt.idx[k]};
       lex_min_into(best[k], v);
@@ -896,18 +923,9 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
     lomag = min(lomag, pt.lomag);
     if constexpr (OCT)
       for (int k = 0; k < 4; k++) dqm[k] = min(dqm[k], pt.dq[k]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
-    amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
-    lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
-    if constexpr (OCT) {
-#pragma unroll
-      for (int q = 0; q < 4; q++) dqm[q] = min(dqm[q], __shfl_xor_sync(0xFFFFFFFFu, dqm[q], o));
-    }
-  }
+  };
+  for (int q = threadIdx.x; q < sd.nchunk1; q += kClsConsumers * 32) fold(w.part[sd.chunk1 + q]);
+  warp_reduce();
   consumers_sync();
   if (lane == 0) {
 #pragma unroll
@@ -920,26 +938,8 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
   consumers_sync();
   if (warp == 0) {
     // the eight warps' results, reduced so that every lane holds the set's
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      if (lane < kClsConsumers) best[k] = red[lane][k];
-      else { best[k].k1 = ~0ull; best[k].k2 = ~0ull; best[k].idx = 0xFFFFFFFFu; }
-    }
-    amin = lane < kClsConsumers ? red_amin[lane] : 0x7FFFFFFFu;
-    lomag = lane < kClsConsumers ? red_lomag[lane] : 0x7FFFFFFFu;
-#pragma unroll
-    for (int q = 0; q < 4; q++) dqm[q] = lane < kClsConsumers ? red_dq[lane][q] : ~0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int k = 0; k < 4; k++) lex_min_into(best[k], lex_shfl(best[k], o));
-      amin = min(amin, __shfl_xor_sync(0xFFFFFFFFu, amin, o));
-      lomag = min(lomag, __shfl_xor_sync(0xFFFFFFFFu, lomag, o));
-      if constexpr (OCT) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) dqm[q] = min(dqm[q], __shfl_xor_sync(0xFFFFFFFFu, dqm[q], o));
-      }
-    }
+    warp0_gather();
+    warp_reduce();
     setup_set_warp<DT>(j, w, s, sd, best, amin, lomag, OCT ? dqm : nullptr);
   } else {
     const int t = threadIdx.x - 32, nt = (kClsConsumers - 1) * 32;
@@ -1007,7 +1007,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_stairs(Job j, Ws w) {
   static_assert(kStairChunk % kThreads == 0, "whole points per thread");
   __shared__ uint64_t lt[4][kStairLB];
   __shared__ uint32_t sw[kWarps];
-  __shared__ float sred[kWarps][4];
+  __shared__ uint32_t sred[kWarps][4];
   __shared__ uint64_t sdq[kWarps][4];
   __shared__ int sidx[4];
   __shared__ float sqx[4], sqy[4];
@@ -1041,44 +1041,47 @@ __global__ void __launch_bounds__(kThreads, 4) k_stairs(Job j, Ws w) {
     const int64_t i = c0 + u * kThreads + tid;
     if (i < c1) view_at<DT>(j, sd.off + i, vx[u], vy[u]);
   }
-  // pass 1: the chunk's extent and the quadrant extremes
+  // pass 1: the chunk's extent and the quadrant extremes (per thread an FP32
+  // score and the first point reaching it; smaller is further into the
+  // quadrant: lower-left x+y, lower-right y-x, upper-right -x-y, upper-left x-y)
   const float inf = __int_as_float(0x7F800000);
   float ext[4] = {inf, -inf, inf, -inf};           // min x, max x, min y, max y
-  uint64_t dq[4] = {~0ull, ~0ull, ~0ull, ~0ull};   // best score key << 32 | index per quadrant
+  float qs[4] = {inf, inf, inf, inf};
+  int qi[4] = {-1, -1, -1, -1};                    // slot u * kThreads + tid of the best point
 #pragma unroll
   for (int u = 0; u < U; u++) {
-    const int64_t i = c0 + u * kThreads + tid;
-    if (i >= c1) continue;
+    if (c0 + u * kThreads + tid >= c1) continue;
     const float X = vx[u], Y = vy[u];
     ext[0] = fminf(ext[0], X); ext[1] = fmaxf(ext[1], X);
     ext[2] = fminf(ext[2], Y); ext[3] = fmaxf(ext[3], Y);
-    // quadrant scores: lower-left x+y, lower-right y-x, upper-right -x-y,
-    // upper-left x-y (smaller is further into the quadrant)
-    dq[0] = min(dq[0], ((uint64_t)f32_order(__fadd_rn(X, Y)) << 32) | (uint32_t)i);
-    dq[1] = min(dq[1], ((uint64_t)f32_order(__fsub_rn(Y, X)) << 32) | (uint32_t)i);
-    dq[2] = min(dq[2], ((uint64_t)f32_order(-__fadd_rn(X, Y)) << 32) | (uint32_t)i);
-    dq[3] = min(dq[3], ((uint64_t)f32_order(__fsub_rn(X, Y)) << 32) | (uint32_t)i);
-  }
+    const float sc[4] = {__fadd_rn(X, Y), __fsub_rn(Y, X), -__fadd_rn(X, Y), __fsub_rn(X, Y)};
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ext[0] = fminf(ext[0], __shfl_xor_sync(0xFFFFFFFFu, ext[0], o));
-    ext[1] = fmaxf(ext[1], __shfl_xor_sync(0xFFFFFFFFu, ext[1], o));
-    ext[2] = fminf(ext[2], __shfl_xor_sync(0xFFFFFFFFu, ext[2], o));
-    ext[3] = fmaxf(ext[3], __shfl_xor_sync(0xFFFFFFFFu, ext[3], o));
-#pragma unroll
-    for (int q = 0; q < 4; q++) dq[q] = min(dq[q], __shfl_xor_sync(0xFFFFFFFFu, dq[q], o));
+    for (int q = 0; q < 4; q++)
+      if (sc[q] < qs[q] || (qi[q] < 0 && !(sc[q] > qs[q]))) { qs[q] = sc[q]; qi[q] = u * kThreads + tid; }
   }
+  // warp minima by order words (redux); the extent ignores NaN
+  uint32_t eo[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint32_t o = f32_order(ext[k]);
+    eo[k] = (k & 1) ? ~__reduce_min_sync(0xFFFFFFFFu, ~o) : __reduce_min_sync(0xFFFFFFFFu, o);
+  }
+  uint64_t dq[4];                                  // order word of the score << 32 | set-local index
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    dq[q] = u64_warp_min(qi[q] < 0 ? ~0ull
+                                   : ((uint64_t)f32_order(qs[q]) << 32) | (uint32_t)(c0 + qi[q]));
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) { sred[warp][k] = ext[k]; sdq[warp][k] = dq[k]; }
+    for (int k = 0; k < 4; k++) { sred[warp][k] = eo[k]; sdq[warp][k] = dq[k]; }
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    float v = sred[0][k];
+    uint32_t v = sred[0][k];
 #pragma unroll
-    for (int q = 1; q < kWarps; q++) v = (k & 1) ? fmaxf(v, sred[q][k]) : fminf(v, sred[q][k]);
-    ext[k] = v;
+    for (int q = 1; q < kWarps; q++) v = (k & 1) ? max(v, sred[q][k]) : min(v, sred[q][k]);
+    ext[k] = f32_unorder(v);
   }
   // one atomic per quadrant and CTA (the set's words take one from every
   // CTA); the control words were cleared before a1, which leaves dq alone
