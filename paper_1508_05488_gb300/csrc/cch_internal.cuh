@@ -915,9 +915,12 @@ __device__ __forceinline__ void move_subslots(const Job& j, const Ws& w, const S
 // griddepcontrol.launch_dependents, measured slower: their CTAs queue for
 // resources the running kernel holds.)
 __device__ __forceinline__ void griddep_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-// The one exception: a1 lets k_stairs be scheduled once its tile loops are
-// done (griddep_release), and k_stairs reduces its sample -- input points
-// only -- before its griddep_enter, while a1's last CTA sets the set up.
+// The one exception: a1 lets k_stairs be scheduled once its tiles are in
+// flight (griddep_release, from the producer after its last copy and from
+// the consumers after their loops), and k_stairs reduces its sample --
+// input points only -- before its griddep_enter, while a1's last CTA sets
+// the set up.  Every k_stairs CTA passes its griddep_enter before it exits,
+// so k_stairs completes after a1 and a2's wait covers both.
 __device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>

@@ -626,6 +626,9 @@ __global__ void __launch_bounds__(kExtBlock, 2) k_extremes(Job j, Ws w) {
                      &st_head[slot]);
       issued = it + 1;
     }
+    // every tile is in flight: k_stairs may be scheduled (it reads none of
+    // a1's results before its griddep_enter)
+    griddep_release();
     if (!ok) {
       // a wait ran out: let the copies already issued land before exiting
       for (int it = max(0, issued - kExtStages); it < issued; it++) {
