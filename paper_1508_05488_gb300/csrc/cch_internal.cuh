@@ -4,7 +4,8 @@
 // Pipeline (Sec. 2.1, steps 1-7), every stage a kernel, every set of points a
 // "set" (a single hull is a batch of one):
 //   a1  k_extremes      four lexicographic extremes + edge set-up (step 1)
-//       k_stairs        dominance tables and box from a sample of each set
+//       k_stairs        dominance tables and box from a sample of each set;
+//                       its sample pass runs during a1's tail
 //   a2  k_classify      quadrilateral test, region routing and dominance
 //                       prefilter; survivors compacted in place per tile
 //                       (steps 2-3)

@@ -20,14 +20,14 @@
 // coordinate and strictly better in the compared one, Q itself lies in R_r
 // (it is on the outer side of edge r and on the inner side of the earlier
 // edges), so P is not an SPA survivor of the full set and dropping it early
-// leaves the SPA survivors -- and the hull -- unchanged.  k_stairs buckets a
-// sample by the sort coordinate (monotone FP32 map) and keeps per bucket the
-// best compared coordinate, as the order word of its FP32 view (the view is
-// non-decreasing in the coordinate, so a strictly larger word means a
-// strictly worse coordinate); the prefix minimum over lower buckets, seeded
-// with the region's first extreme, gives for every bucket a word such that
-// any region point of that bucket with a larger word is dominated by a
-// sample point of a strictly lower bucket.
+// leaves the SPA survivors -- and the hull -- unchanged.  k_stairs buckets
+// the staircase steps of a sample by the sort coordinate (monotone FP32 map)
+// and keeps per bucket the best compared coordinate, as the order word of
+// its FP32 view (the view is non-decreasing in the coordinate, so a strictly
+// larger word means a strictly worse coordinate); the prefix minimum over
+// lower buckets, seeded with the region's first extreme, gives for every
+// bucket a word such that any region point of that bucket with a larger word
+// is dominated by a sample point of a strictly lower bucket.
 //
 // Dominance box.  The same argument in all four quadrants at once: k_stairs
 // also picks the sample point furthest into each quadrant (smallest x+y,
