@@ -10,7 +10,9 @@ end to end against the oracle):
   is not NaN (+-Inf included), equal for -0.0 and +0.0, and NaN or +-Inf only
   for values the domain check rejects at the top (|c| >= 2^1017, Inf, NaN);
   the warp's integer key bound maps back to those bits exactly;
-* cch_hull_f32soa widens float32 to float64 from the IEEE bit fields.
+* cch_hull_f32soa widens float32 to float64 from the IEEE bit fields;
+* a1 reduces its lexicographic keys across a warp one 32-bit word at a time
+  (the minimum of each word over the lanes still tied on the earlier ones).
 """
 import numpy as np
 
@@ -119,3 +121,43 @@ def test_widening_matches_ieee_conversion():
             assert np.isnan(w)
         else:
             assert w == r and np.signbit(w) == np.signbit(r), hex(x)
+
+
+# ---------------------------------------------------------------------------
+# a1's warp minima: one redux.sync minimum per 32-bit word, each over the
+# lanes still tied on the earlier words, must give the lexicographic minimum
+# of (k1, k2, idx) -- ties, all-ones words and all-tied warps included.
+
+def warp_lex_min(k1, k2, idx):
+    """The word-by-word reduction of one warp (32 lanes), as lex_warp_min does."""
+    words = [k1 >> np.uint64(32), k1 & np.uint64(0xFFFFFFFF), k2 >> np.uint64(32), k2 & np.uint64(0xFFFFFFFF),
+             idx.astype(np.uint64)]
+    tied = np.ones(32, bool)
+    out = []
+    for wd in words:
+        m = np.where(tied, wd, np.uint64(0xFFFFFFFF)).min()
+        tied &= wd == m
+        out.append(int(m))
+    return (out[0] << 32 | out[1], out[2] << 32 | out[3], out[4])
+
+
+def test_word_by_word_warp_minimum_is_the_lexicographic_minimum():
+    rng = np.random.default_rng(5)
+    for t in range(3000):
+        # few distinct words so that ties reach every level
+        pool = np.array([0, 1, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFE, 0xFFFFFFFF], dtype=np.uint64)
+        w = pool[rng.integers(0, len(pool) if t % 3 else 2, size=(32, 4))]
+        k1 = (w[:, 0] << np.uint64(32)) | w[:, 1]
+        k2 = (w[:, 2] << np.uint64(32)) | w[:, 3]
+        idx = pool[rng.integers(0, len(pool), size=32)].astype(np.uint32)
+        want = min(zip(k1.tolist(), k2.tolist(), idx.tolist()))
+        assert warp_lex_min(k1, k2, idx) == want
+
+
+def test_word_by_word_warp_minimum_of_64_bit_keys():
+    rng = np.random.default_rng(6)
+    for _ in range(2000):
+        v = rng.integers(0, 4, size=32).astype(np.uint64) << np.uint64(32) | rng.integers(0, 3, size=32).astype(np.uint64)
+        hi = (v >> np.uint64(32)).min()
+        lo = np.where((v >> np.uint64(32)) == hi, v & np.uint64(0xFFFFFFFF), np.uint64(0xFFFFFFFF)).min()
+        assert int(hi) << 32 | int(lo) == int(v.min())

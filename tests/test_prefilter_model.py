@@ -176,3 +176,43 @@ def test_planted_inclusive_prefix_is_caught(cases):
         drop = dropped(X, Y, m["region"], tabs)
         hit += sum(len(set(drop[r].tolist()) & spa[r]) for r in range(4))
     assert hit > 0
+
+
+def chunk_steps_skipping(X, Y, r, nloc):
+    """chunk_steps without the points that the chunk's quadrant extreme of
+    region r beats strictly in both coordinates (R1 lower-left, R2
+    lower-right, R3 upper-right, R4 upper-left), as k_stairs skips them."""
+    sx, sy = X.astype(np.float64), Y.astype(np.float64)
+    score = (sx + sy, sy - sx, -sx - sy, sx - sy)[r]
+    q = int(np.argmin(score))
+    qx, qy = X[q], Y[q]
+    bx = (qx < X) if r in (0, 3) else (qx > X)
+    by = (qy < Y) if r < 2 else (qy > Y)
+    keep = ~(bx & by)
+    u = sort_u(X, Y, r)
+    a, b = np.float32(u.min()), np.float32(u.max())      # the map is the whole chunk's
+    wd = np.float32(b - a)
+    scale = np.float32(nloc) / wd if wd > 0 else np.float32(0)
+    bk = bucket(u, a, scale, nloc)[keep]
+    uu, v = u[keep], cmp_word(X, Y, r)[keep]
+    order = np.lexsort((uu, v, bk))
+    first = np.ones(len(order), bool)
+    first[1:] = bk[order][1:] != bk[order][:-1]
+    rep = order[first]
+    vv = v[rep]
+    steps = np.ones(len(rep), bool)
+    steps[1:] = vv[1:] < np.minimum.accumulate(vv)[:-1]
+    return uu[rep[steps]], vv[steps]
+
+
+@pytest.mark.parametrize("name", [s[0] for s in SETS])
+def test_skipping_points_beaten_by_the_quadrant_extreme_keeps_the_steps(cases, name):
+    p, m, X, Y, spa = cases[name]
+    n = len(X)
+    for c0 in range(n - 8192, n, 2048):
+        cx, cy = X[c0:c0 + 2048], Y[c0:c0 + 2048]
+        for r in range(4):
+            a = chunk_steps(cx, cy, r, 512)
+            b = chunk_steps_skipping(cx, cy, r, 512)
+            assert np.array_equal(a[1], b[1]), (name, c0, r)
+            assert np.array_equal(a[0], b[0]), (name, c0, r)
