@@ -790,7 +790,10 @@ def main():
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": hbm_src,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_ms_per_launch": dom_ms,
-                "stage_ms_per_hull": stage_all}
+                "stage_ms_per_hull": stage_all,
+                "stage_note": "stage times come from events recorded between the launches, which keep "
+                              "k_stairs from overlapping a1's tail; a hull without events (per_set.*.hull.ms) "
+                              "takes less than the sum of its stages"}
     # the whole step against the method's floor: two reads of every input
     # point (the extremes must be known before the classification)
     step_bytes = 2 * 16.0 * args.n * len(kinds)
