@@ -12,7 +12,10 @@ end to end against the oracle):
   the warp's integer key bound maps back to those bits exactly;
 * cch_hull_f32soa widens float32 to float64 from the IEEE bit fields;
 * a1 reduces its lexicographic keys across a warp one 32-bit word at a time
-  (the minimum of each word over the lanes still tied on the earlier ones).
+  (the minimum of each word over the lanes still tied on the earlier ones);
+* the sort and SPA keys preserve the order of the coordinates (-0.0 and
+  +0.0 equal), and a2's three-operation FP32 view equals the truncated view
+  for every magnitude in [2^-126, 2^60].
 """
 import numpy as np
 
@@ -161,3 +164,61 @@ def test_word_by_word_warp_minimum_of_64_bit_keys():
         hi = (v >> np.uint64(32)).min()
         lo = np.where((v >> np.uint64(32)) == hi, v & np.uint64(0xFFFFFFFF), np.uint64(0xFFFFFFFF)).min()
         assert int(hi) << 32 | int(lo) == int(v.min())
+
+
+# ---------------------------------------------------------------------------
+# Order-preserving keys of the sort and SPA stages, and a2's three-operation
+# FP32 view of sets whose coordinates all have magnitude in [2^-126, 2^60].
+
+def key_f64(x):
+    """key_f64 on the float64 bits: -0.0 made +0.0, then the sign-magnitude
+    to unsigned order map."""
+    b = np.asarray(x, dtype=np.float64).view(np.uint64).copy()
+    b[b == np.uint64(0x8000000000000000)] = np.uint64(0)
+    neg = (b >> np.uint64(63)) != 0
+    return np.where(neg, ~b, b | np.uint64(0x8000000000000000))
+
+
+def key_i32(v):
+    return (np.asarray(v, dtype=np.int32).view(np.uint32) ^ np.uint32(0x80000000)).astype(np.uint64)
+
+
+def test_float64_and_int32_keys_preserve_order_and_equality():
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(3000) * 10.0 ** rng.integers(-300, 300, 3000),
+                        [0.0, -0.0, 5e-324, -5e-324, np.inf, -np.inf, 1.0, np.nextafter(1.0, 2.0)]])
+    k = key_f64(x)
+    i, j = rng.integers(0, len(x), 20000), rng.integers(0, len(x), 20000)
+    assert np.array_equal(k[i] < k[j], x[i] < x[j])
+    assert np.array_equal(k[i] == k[j], x[i] == x[j])
+    v = np.concatenate([rng.integers(-2 ** 31, 2 ** 31, 3000), [-2 ** 31, -1, 0, 1, 2 ** 31 - 1]]).astype(np.int64)
+    kv = key_i32(v)
+    i, j = rng.integers(0, len(v), 20000), rng.integers(0, len(v), 20000)
+    assert np.array_equal(kv[i] < kv[j], v[i] < v[j])
+    # the descending regions complement the key: the order reverses
+    assert np.array_equal(~k[i] < ~k[j], x[i] > x[j])
+
+
+def view_short(x):
+    """f64_view_short: the top word rebiased by subtraction on the signed word
+    and funnel-shifted with the low word's three leading bits, sign put back."""
+    b = np.asarray(x, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.uint64)
+    lo = (b & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    t = (hi - np.uint64(0x38000000)) & np.uint64(0xFFFFFFFF)
+    shifted = ((t << np.uint64(3)) | (lo >> np.uint64(29))) & np.uint64(0xFFFFFFFF)
+    return (shifted | (hi & np.uint64(0x80000000))).astype(np.uint32).view(np.float32)
+
+
+def test_short_view_equals_the_truncated_view_in_its_domain():
+    rng = np.random.default_rng(12)
+    mag = 2.0 ** rng.uniform(-126, 60, 20000)
+    x = np.where(rng.integers(0, 2, 20000) == 1, -mag, mag)
+    x = np.concatenate([x, [2.0 ** -126, -(2.0 ** -126), np.nextafter(2.0 ** 60, 0), -np.nextafter(2.0 ** 60, 0)]])
+    # f64_trunc_f32: exponent rebiased on the magnitude, significand truncated
+    b = x.view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.int64)
+    lo = (b & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    t = (hi & 0x7FFFFFFF) - 0x38000000
+    full = np.where(t < 0, hi & 0x80000000, (hi & 0x80000000) | (((t << 3) | (lo >> 29)) & 0xFFFFFFFF))
+    assert np.array_equal(view_short(x).view(np.uint32), full.astype(np.uint32))
