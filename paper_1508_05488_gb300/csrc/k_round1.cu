@@ -989,10 +989,10 @@ __device__ __forceinline__ int bucket_of(float u, float lo, float scale) {
 
 // k_stairs: the dominance table of every set from the sample.  Each CTA
 // takes kStairChunk sample points (eight per thread, loaded once and held in
-// registers).  Before its griddep_enter it reads only
-// input points, so it runs during a1's tail (a1 releases it after its tile
-// loops): pass 1 finds the chunk's extent and the quadrant extremes of the
-// dominance box, pass 2 keeps, per region r and bucket of the chunk's own map
+// registers).  Before its griddep_enter it reads only input points, so it
+// runs during a1's tail (a1 releases it once its tiles are in flight): pass
+// 1 finds the chunk's extent and the quadrant extremes of the dominance box,
+// pass 2 keeps, per region r and bucket of the chunk's own map
 // (kStairLB buckets over the extent of the region's sort coordinate u =
 // sort_u), the smallest (compared word v = cmp_view_order) << 32 | (order
 // word of u), and the buckets whose v is below every lower bucket's are the
